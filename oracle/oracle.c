@@ -1,0 +1,447 @@
+/*
+ * FP64 CPU oracle: D3Q19 MRT lattice Boltzmann with Guo forcing, halfway
+ * bounceback and periodic boundaries, after Rao & Schaefer (arXiv:1902.11193).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline arm, never by the product library.  It shares no
+ * code with the CUDA path.  Every operation is written out in its plainest
+ * form: a dense 19x19 moment matrix M, its inverse M^T D^-1, the forcing
+ * populations of eq. (Guo_Forcing) multiplied by M, and a two-array pull
+ * stream.  OpenMP only splits independent z-planes; every sum is taken in a
+ * fixed order, so results do not depend on the thread count.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 19
+#define RHO0 1.0
+
+/* D3Q19 velocity set (Sec. 2.1).  The paper names the lattice but prints no
+ * ordering; rest first, then the six axis links, then the twelve edges. */
+static const int CV[Q][3] = {
+    {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double W[Q];
+static int OPP[Q];
+static double M[Q][Q];    /* m = M f */
+static double MINV[Q][Q]; /* f = MINV m = M^T D^-1 m */
+static int initialised = 0;
+
+static void init_tables(void) {
+    if (initialised) return;
+    for (int i = 0; i < Q; ++i) {
+        int c2 = CV[i][0] * CV[i][0] + CV[i][1] * CV[i][1] + CV[i][2] * CV[i][2];
+        /* weights implied by eq. (BGK-EDF) with c_s^2 = 1/3 on D3Q19 */
+        W[i] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        for (int j = 0; j < Q; ++j)
+            if (CV[j][0] == -CV[i][0] && CV[j][1] == -CV[i][1] && CV[j][2] == -CV[i][2])
+                OPP[i] = j;
+    }
+    /* Rows of M: the orthogonal polynomial basis of d'Humieres et al. (2002)
+     * in the moment order of Sec. 2.2.1:
+     * (rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz,
+     *  pxz, mx, my, mz). */
+    for (int i = 0; i < Q; ++i) {
+        double x = CV[i][0], y = CV[i][1], z = CV[i][2];
+        double c2 = x * x + y * y + z * z;
+        M[0][i] = 1.0;
+        M[1][i] = 19.0 * c2 - 30.0;
+        M[2][i] = (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+        M[3][i] = x;
+        M[4][i] = (5.0 * c2 - 9.0) * x;
+        M[5][i] = y;
+        M[6][i] = (5.0 * c2 - 9.0) * y;
+        M[7][i] = z;
+        M[8][i] = (5.0 * c2 - 9.0) * z;
+        M[9][i] = 3.0 * x * x - c2;
+        M[10][i] = (3.0 * c2 - 5.0) * (3.0 * x * x - c2);
+        M[11][i] = y * y - z * z;
+        M[12][i] = (3.0 * c2 - 5.0) * (y * y - z * z);
+        M[13][i] = x * y;
+        M[14][i] = y * z;
+        M[15][i] = x * z;
+        M[16][i] = x * (y * y - z * z);
+        M[17][i] = y * (z * z - x * x);
+        M[18][i] = z * (x * x - y * y);
+    }
+    /* The rows are orthogonal, so M^-1 = M^T D^-1 with D = diag(M M^T). */
+    for (int k = 0; k < Q; ++k) {
+        double d = 0.0;
+        for (int i = 0; i < Q; ++i) d += M[k][i] * M[k][i];
+        for (int i = 0; i < Q; ++i) MINV[i][k] = M[k][i] / d;
+    }
+    initialised = 1;
+}
+
+void ora_lattice(int32_t c[Q * 3], double w[Q], int32_t opp[Q]) {
+    init_tables();
+    for (int i = 0; i < Q; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = CV[i][a];
+        w[i] = W[i];
+        opp[i] = OPP[i];
+    }
+}
+
+void ora_moment_matrix(double Mout[Q * Q]) {
+    init_tables();
+    for (int k = 0; k < Q; ++k)
+        for (int i = 0; i < Q; ++i) Mout[k * Q + i] = M[k][i];
+}
+
+/* Table 2.  s_nu = 1/tau in every set.  Kinetic rates:
+ *   A: every other non-conserved rate 8(2 - s_nu)/(8 - s_nu)
+ *   B: even rates s_nu; s_q = s_m = 8(2 - s_nu)/(8 - s_nu)
+ *   C: s_e 1.19, s_eps 1.4, s_q 1.2, s_pi 1.4, s_m 1.98 (d'Humieres 2002)
+ *   D: even rates s_nu; s_q = 8(2 - s_nu)/(8 - s_nu), s_m = 4(2 - s_nu)/(4 + s_nu)
+ *   E: even rates s_nu; s_q = s_m = 2(2 - s_nu)/(4 Lambda s_nu - s_nu + 2),
+ *      i.e. eq. (Magic param) held at Lambda
+ *   SRT: every rate 1/tau (the BGK limit of Sec. 2.2.2). */
+int ora_rates(int set, double tau, double Lambda, double s[Q]) {
+    if (!(tau > 0.5)) return -1;
+    double sn = 1.0 / tau;
+    double se, seps, sq, spi, sm;
+    double k8 = 8.0 * (2.0 - sn) / (8.0 - sn);
+    switch (set) {
+    case ORA_SET_A: se = seps = sq = spi = sm = k8; break;
+    case ORA_SET_B: se = seps = spi = sn; sq = sm = k8; break;
+    case ORA_SET_C: se = 1.19; seps = 1.4; sq = 1.2; spi = 1.4; sm = 1.98; break;
+    case ORA_SET_D:
+        se = seps = spi = sn;
+        sq = k8;
+        sm = 4.0 * (2.0 - sn) / (4.0 + sn);
+        break;
+    case ORA_SET_E:
+        if (!(Lambda > 0.0)) return -1;
+        se = seps = spi = sn;
+        sq = sm = 2.0 * (2.0 - sn) / (4.0 * Lambda * sn - sn + 2.0);
+        break;
+    case ORA_SET_SRT: se = seps = sq = spi = sm = sn; break;
+    default: return -1;
+    }
+    /* S = diag(0, se, seps, 0, sq, 0, sq, 0, sq, snu, spi, snu, spi, snu, snu,
+     *          snu, sm, sm, sm), eq. (MRT params) */
+    double t[Q] = {0.0, se, seps, 0.0, sq, 0.0, sq, 0.0, sq, sn,
+                   spi, sn, spi, sn, sn, sn, sm, sm, sm};
+    for (int k = 0; k < Q; ++k) s[k] = t[k];
+    return 0;
+}
+
+/* eq. (MRT Equi) with rho0 = 1, read so that m^eq = M f^eq: m1 carries -11 rho
+ * and m9 carries 2 jx^2 - jy^2 - jz^2 (the printed +11 rho and jx^2 - jy^2 -
+ * jz^2 do not satisfy it), m10 = -m9/2, m12 = -m11/2.  With linear != 0 the
+ * quadratic terms are dropped (the Stokes simplification of Sec. 2.2.1). */
+void ora_meq(double rho, const double j[3], int linear, double meq[Q]) {
+    double q = linear ? 0.0 : 1.0 / RHO0;
+    double jx = j[0], jy = j[1], jz = j[2];
+    double jj = jx * jx + jy * jy + jz * jz;
+    meq[0] = rho;
+    meq[1] = -11.0 * rho + 19.0 * q * jj;
+    meq[2] = 3.0 * rho - 11.0 / 2.0 * q * jj;
+    meq[3] = jx;
+    meq[4] = -2.0 / 3.0 * jx;
+    meq[5] = jy;
+    meq[6] = -2.0 / 3.0 * jy;
+    meq[7] = jz;
+    meq[8] = -2.0 / 3.0 * jz;
+    meq[9] = q * (2.0 * jx * jx - jy * jy - jz * jz);
+    meq[10] = -0.5 * meq[9];
+    meq[11] = q * (jy * jy - jz * jz);
+    meq[12] = -0.5 * meq[11];
+    meq[13] = q * jx * jy;
+    meq[14] = q * jy * jz;
+    meq[15] = q * jx * jz;
+    meq[16] = meq[17] = meq[18] = 0.0;
+}
+
+/* eq. (Guo_Forcing) with c_s^2 = 1/3:
+ * F_i = w_i [ (c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4 ] . F.
+ * linear != 0 drops the terms in u. */
+void ora_guo_populations(const double u[3], const double F[3], int linear, double Fi[Q]) {
+    init_tables();
+    double ul[3] = {linear ? 0.0 : u[0], linear ? 0.0 : u[1], linear ? 0.0 : u[2]};
+    for (int i = 0; i < Q; ++i) {
+        double cu = CV[i][0] * ul[0] + CV[i][1] * ul[1] + CV[i][2] * ul[2];
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a)
+            acc += (3.0 * (CV[i][a] - ul[a]) + 9.0 * cu * CV[i][a]) * F[a];
+        Fi[i] = W[i] * acc;
+    }
+}
+
+/* m^F = M . F_i: the paper computes the forcing populations first and then
+ * multiplies by M (Sec. 2.2.1). */
+void ora_force_moments(const double u[3], const double F[3], int linear, double mF[Q]) {
+    double Fi[Q];
+    ora_guo_populations(u, F, linear, Fi);
+    for (int k = 0; k < Q; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) acc += M[k][i] * Fi[i];
+        mF[k] = acc;
+    }
+}
+
+/* One node of eq. (MRT-LBE):
+ *   m = M f;  rho = m0;  j = (m3, m5, m7) + F/2 (the shifted velocity of
+ *   Sec. 2.2.1, rho0 u = sum_i c_i f_i + F/2);  u = j / rho0;
+ *   m*_k = m_k - s_k (m_k - m^eq_k) + (1 - s_k/2) m^F_k;  f* = M^-1 m*. */
+void ora_collide(const double f[Q], const double s[Q], const double F[3], int linear,
+                 double fout[Q]) {
+    init_tables();
+    double m[Q], meq[Q], mF[Q], ms[Q];
+    for (int k = 0; k < Q; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) acc += M[k][i] * f[i];
+        m[k] = acc;
+    }
+    double rho = m[0];
+    double j[3] = {m[3] + 0.5 * F[0], m[5] + 0.5 * F[1], m[7] + 0.5 * F[2]};
+    double u[3] = {j[0] / RHO0, j[1] / RHO0, j[2] / RHO0};
+    ora_meq(rho, j, linear, meq);
+    ora_force_moments(u, F, linear, mF);
+    for (int k = 0; k < Q; ++k) ms[k] = m[k] - s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * s[k]) * mF[k];
+    for (int i = 0; i < Q; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < Q; ++k) acc += MINV[i][k] * ms[k];
+        fout[i] = acc;
+    }
+}
+
+static int wrapi(int v, int L) {
+    int r = v % L;
+    return r < 0 ? r + L : r;
+}
+
+int64_t ora_links(const uint8_t *mask, const int32_t dims[3], int32_t *fluid_idx,
+                  int32_t *nbr, uint32_t *bbmask, int64_t links[Q]) {
+    init_tables();
+    int Lx = dims[0], Ly = dims[1], Lz = dims[2];
+    int64_t N = (int64_t)Lx * Ly * Lz;
+    int32_t *f_of_node = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    int64_t Nf = 0;
+    for (int64_t n = 0; n < N; ++n) f_of_node[n] = mask[n] ? -1 : (int32_t)Nf++;
+    if (links)
+        for (int i = 0; i < Q; ++i) links[i] = 0;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                int64_t n = x + (int64_t)Lx * (y + (int64_t)Ly * z);
+                if (mask[n]) continue;
+                int32_t fi = f_of_node[n];
+                if (fluid_idx) fluid_idx[fi] = (int32_t)n;
+                uint32_t bits = 0;
+                for (int i = 1; i < Q; ++i) {
+                    int xs = wrapi(x - CV[i][0], Lx), ys = wrapi(y - CV[i][1], Ly),
+                        zs = wrapi(z - CV[i][2], Lz);
+                    int64_t ns = xs + (int64_t)Lx * (ys + (int64_t)Ly * zs);
+                    int32_t src = f_of_node[ns];
+                    if (src < 0) {
+                        bits |= 1u << i;
+                        if (links) links[i]++;
+                    }
+                    if (nbr) nbr[(int64_t)(i - 1) * Nf + fi] = src;
+                }
+                if (bbmask) bbmask[fi] = bits;
+            }
+    free(f_of_node);
+    return Nf;
+}
+
+struct ora_solver {
+    int Lx, Ly, Lz;
+    int64_t N;
+    uint8_t *solid;
+    double *f, *ftmp; /* [Q][N], post-collision state */
+    double s[Q], F[3];
+    int linear;
+    int64_t steps;
+};
+
+ora_solver *ora_create(const uint8_t *mask, const int32_t dims[3], const double s[Q],
+                       const double F[3], int linear) {
+    init_tables();
+    if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return NULL;
+    ora_solver *h = (ora_solver *)calloc(1, sizeof(ora_solver));
+    h->Lx = dims[0];
+    h->Ly = dims[1];
+    h->Lz = dims[2];
+    h->N = (int64_t)h->Lx * h->Ly * h->Lz;
+    h->solid = (uint8_t *)malloc((size_t)h->N);
+    memcpy(h->solid, mask, (size_t)h->N);
+    h->f = (double *)malloc(sizeof(double) * Q * (size_t)h->N);
+    h->ftmp = (double *)malloc(sizeof(double) * Q * (size_t)h->N);
+    /* initial state: rest at rho0, f_i = w_i (the paper does not state one) */
+    for (int i = 0; i < Q; ++i)
+        for (int64_t n = 0; n < h->N; ++n) h->f[i * h->N + n] = W[i];
+    for (int k = 0; k < Q; ++k) h->s[k] = s[k];
+    for (int a = 0; a < 3; ++a) h->F[a] = F[a];
+    h->linear = linear;
+    return h;
+}
+
+void ora_destroy(ora_solver *h) {
+    if (!h) return;
+    free(h->solid);
+    free(h->f);
+    free(h->ftmp);
+    free(h);
+}
+
+/* Pull stream with halfway bounceback: f_i(x) = f*_i(x - c_i) when x - c_i
+ * (periodic wrap) is fluid, else f*_opp(i)(x) (eq. LBE with the bounceback
+ * rule applied at the half-link). */
+static void pull(const ora_solver *h, const double *fs, int x, int y, int z, double fl[Q]) {
+    int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+    for (int i = 0; i < Q; ++i) {
+        int xs = wrapi(x - CV[i][0], h->Lx), ys = wrapi(y - CV[i][1], h->Ly),
+            zs = wrapi(z - CV[i][2], h->Lz);
+        int64_t ns = xs + (int64_t)h->Lx * (ys + (int64_t)h->Ly * zs);
+        fl[i] = h->solid[ns] ? fs[OPP[i] * h->N + n] : fs[i * h->N + ns];
+    }
+}
+
+/* Velocity of a streamed node: u = (sum_i c_i f_i + F/2) / rho0. */
+static void node_velocity(const ora_solver *h, const double fl[Q], double u[3]) {
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) acc += CV[i][a] * fl[i];
+        u[a] = (acc + 0.5 * h->F[a]) / RHO0;
+    }
+}
+
+/* Sums per z-plane, then over planes in order: fixed summation order. */
+static void one_step(ora_solver *h, double U[3]) {
+    double *plane = U ? (double *)calloc(3 * (size_t)h->Lz, sizeof(double)) : NULL;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < h->Lz; ++z) {
+        double fl[Q], fo[Q], u[3];
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) {
+                    for (int i = 0; i < Q; ++i) h->ftmp[i * h->N + n] = h->f[i * h->N + n];
+                    continue;
+                }
+                pull(h, h->f, x, y, z, fl);
+                if (plane) {
+                    node_velocity(h, fl, u);
+                    for (int a = 0; a < 3; ++a) plane[3 * z + a] += u[a];
+                }
+                ora_collide(fl, h->s, h->F, h->linear, fo);
+                for (int i = 0; i < Q; ++i) h->ftmp[i * h->N + n] = fo[i];
+            }
+    }
+    double *t = h->f;
+    h->f = h->ftmp;
+    h->ftmp = t;
+    h->steps++;
+    if (U) {
+        for (int a = 0; a < 3; ++a) {
+            double acc = 0.0;
+            for (int z = 0; z < h->Lz; ++z) acc += plane[3 * z + a];
+            U[a] = acc / (double)h->N;
+        }
+        free(plane);
+    }
+}
+
+void ora_step(ora_solver *h, int64_t n, double U[3]) {
+    for (int64_t t = 0; t < n; ++t) one_step(h, t == n - 1 ? U : NULL);
+}
+
+void ora_velocity(ora_solver *h, double *u) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < h->Lz; ++z) {
+        double fl[Q], v[3];
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) {
+                    for (int a = 0; a < 3; ++a) u[a * h->N + n] = 0.0;
+                    continue;
+                }
+                pull(h, h->f, x, y, z, fl);
+                node_velocity(h, fl, v);
+                for (int a = 0; a < 3; ++a) u[a * h->N + n] = v[a];
+            }
+    }
+}
+
+void ora_mean_velocity(ora_solver *h, double U[3]) {
+    double *u = (double *)malloc(sizeof(double) * 3 * (size_t)h->N);
+    ora_velocity(h, u);
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int z = 0; z < h->Lz; ++z) {
+            double p = 0.0;
+            for (int64_t r = 0; r < (int64_t)h->Lx * h->Ly; ++r)
+                p += u[a * h->N + (int64_t)z * h->Lx * h->Ly + r];
+            acc += p;
+        }
+        U[a] = acc / (double)h->N;
+    }
+    free(u);
+}
+
+void ora_get_f(ora_solver *h, double *f) { memcpy(f, h->f, sizeof(double) * Q * (size_t)h->N); }
+void ora_set_f(ora_solver *h, const double *f) {
+    memcpy(h->f, f, sizeof(double) * Q * (size_t)h->N);
+}
+int64_t ora_steps_done(ora_solver *h) { return h->steps; }
+
+/* Stopping rule of eq. (convergence): the relative change of k (equivalently
+ * of the mean velocity along the drive, k = nu U / F) between consecutive
+ * steps.  It is evaluated on the last two steps of every chunk of K steps. */
+int ora_run_to_convergence(ora_solver *h, double tol, int64_t K, int64_t max_steps,
+                           int64_t *steps, double U[3]) {
+    int d = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(h->F[a]) > fabs(h->F[d])) d = a;
+    if (K < 1) K = 1;
+    int64_t done = 0;
+    double Ua[3] = {NAN, NAN, NAN}, Ub[3] = {NAN, NAN, NAN};
+    int rc = 1;
+    while (done < max_steps) {
+        int64_t chunk = K;
+        if (chunk > max_steps - done) chunk = max_steps - done;
+        if (K == 1) {
+            for (int a = 0; a < 3; ++a) Ua[a] = Ub[a];
+            ora_step(h, 1, Ub);
+        } else {
+            if (chunk >= 2) ora_step(h, chunk - 2, NULL);
+            if (chunk >= 2) ora_step(h, 1, Ua);
+            else for (int a = 0; a < 3; ++a) Ua[a] = Ub[a];
+            ora_step(h, 1, Ub);
+        }
+        done += chunk;
+        if (!isfinite(Ub[0]) || !isfinite(Ub[1]) || !isfinite(Ub[2])) { rc = 2; break; }
+        if (isfinite(Ua[d]) && fabs(Ub[d] - Ua[d]) <= tol * fabs(Ub[d])) { rc = 0; break; }
+    }
+    if (steps) *steps = done;
+    if (U)
+        for (int a = 0; a < 3; ++a) U[a] = Ub[a];
+    return rc;
+}
+
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int ora_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,79 @@
+/*
+ * FP64 CPU oracle for the D3Q19-MRT lattice Boltzmann permeability solver of
+ * Rao & Schaefer, "Lattice Boltzmann Models for Micro-tomographic
+ * Pore-spaces" (arXiv:1902.11193).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow reference that the CUDA
+ * path is checked against.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load it; the product library never does.
+ * It shares no code, header, table or helper with the CUDA path.
+ *
+ * Conventions (the paper prints none of these; the readings are listed in the
+ * design notes):
+ *   velocities  i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
+ *               (-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),
+ *               (-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1)
+ *   node index  n = x + Lx*(y + Ly*z); mask 1 = solid, 0 = fluid
+ *   populations f[i*N + n], unshifted (rest state f_i = w_i, rho0 = 1)
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_SET_A = 0, ORA_SET_B, ORA_SET_C, ORA_SET_D, ORA_SET_E, ORA_SET_SRT };
+
+/* Lattice constants: c[19][3], w[19], opposite[19]. */
+void ora_lattice(int32_t c[19 * 3], double w[19], int32_t opp[19]);
+/* Dense moment matrix M[19][19] (row k = moment k, Sec. 2.2.1 order). */
+void ora_moment_matrix(double M[19 * 19]);
+/* Relaxation rates s[19] of Table 2 for (set, tau, Lambda). Returns 0 or -1. */
+int ora_rates(int set, double tau, double Lambda, double s[19]);
+/* Equilibrium moments, eq. (MRT Equi), for density rho and shifted momentum j. */
+void ora_meq(double rho, const double j[3], int linear, double meq[19]);
+/* Guo forcing populations, eq. (Guo_Forcing), for velocity u and force F. */
+void ora_guo_populations(const double u[3], const double F[3], int linear, double Fi[19]);
+/* Forcing moments m^F = M . F_i (the literal matrix-vector product). */
+void ora_force_moments(const double u[3], const double F[3], int linear, double mF[19]);
+/* One MRT collision of a single node: f -> f*, eq. (MRT-LBE). */
+void ora_collide(const double f[19], const double s[19], const double F[3], int linear,
+                 double fout[19]);
+
+/* Link table of a mask: fluid list, pull neighbours (x - c_i) and bounceback
+ * bits.  fluid_idx[Nf], nbr[18][Nf] (entry for direction i at (i-1)*Nf + n,
+ * -1 where x - c_i is solid), bbmask[Nf] (bit i set iff x - c_i is solid),
+ * links[19] (per-direction count of bounceback links).  Any output may be
+ * NULL.  Returns Nf. */
+int64_t ora_links(const uint8_t *mask, const int32_t dims[3], int32_t *fluid_idx,
+                  int32_t *nbr, uint32_t *bbmask, int64_t links[19]);
+
+typedef struct ora_solver ora_solver;
+ora_solver *ora_create(const uint8_t *mask, const int32_t dims[3], const double s[19],
+                       const double F[3], int linear);
+void ora_destroy(ora_solver *h);
+/* n pull-stream + collide steps.  If U is non-NULL it receives the mean
+ * velocity of the streamed state collided in the last step. */
+void ora_step(ora_solver *h, int64_t n, double U[3]);
+/* Mean velocity (over all N voxels, solids count as 0) of the current state
+ * after streaming, without advancing: U = (1/N) sum_fluid (sum_i c_i f_i + F/2). */
+void ora_mean_velocity(ora_solver *h, double U[3]);
+/* Velocity field u[3][N] of the streamed current state (0 in solids). */
+void ora_velocity(ora_solver *h, double *u);
+void ora_get_f(ora_solver *h, double *f);
+void ora_set_f(ora_solver *h, const double *f);
+int64_t ora_steps_done(ora_solver *h);
+/* Steps in chunks of K until |U_b - U_a| <= tol |U_b| for the mean x-velocity
+ * of the last two steps of a chunk, or max_steps.  Returns 0 converged, 1 not
+ * converged, 2 non-finite. */
+int ora_run_to_convergence(ora_solver *h, double tol, int64_t K, int64_t max_steps,
+                           int64_t *steps, double U[3]);
+void ora_set_threads(int n);
+int ora_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,77 @@
+"""In-tree build of the package's native libraries.
+
+``liblbm_gb300.so``: the CUDA kernels and the C ABI, compiled by nvcc for
+sm_103a only.  ``libgeom.so``: the seeded voxel-image generators (plain C).
+Both land in ``paper_1902_11193_gb300/lib/``.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+LIBDIR = os.path.join(PKG, "lib")
+INCLUDE = os.path.join(ROOT, "include")
+
+GEOM_SO = os.path.join(LIBDIR, "libgeom.so")
+LBM_SO = os.path.join(LIBDIR, "liblbm_gb300.so")
+
+CUDA_SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_links.cu"]
+CUDA_HEADERS = ["lbm_internal.cuh", "lbm_collide.cuh"]
+NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    p = os.path.join(home, "bin", "nvcc")
+    return p if os.path.exists(p) else "nvcc"
+
+
+def _stale(out: str, deps: list[str]) -> bool:
+    if not os.path.exists(out):
+        return True
+    t = os.path.getmtime(out)
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def build_geometry(force: bool = False) -> str:
+    src = os.path.join(CSRC, "geometry.c")
+    if force or _stale(GEOM_SO, [src]):
+        os.makedirs(LIBDIR, exist_ok=True)
+        tmp = GEOM_SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE",
+                        "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, GEOM_SO)
+    return GEOM_SO
+
+
+def build_lbm(force: bool = False, extra_flags: list[str] | None = None) -> str:
+    srcs = [os.path.join(CSRC, s) for s in CUDA_SOURCES]
+    deps = srcs + [os.path.join(CSRC, h) for h in CUDA_HEADERS] + [os.path.join(INCLUDE, "lbm.h")]
+    if not (force or _stale(LBM_SO, deps)):
+        return LBM_SO
+    os.makedirs(LIBDIR, exist_ok=True)
+    objdir = os.path.join(LIBDIR, "obj")
+    os.makedirs(objdir, exist_ok=True)
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *NVCC_ARCH,
+             "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr", *(extra_flags or [])]
+
+    def compile_one(src: str) -> str:
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        subprocess.run([_nvcc(), *flags, "-c", src, "-o", obj], check=True)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LBM_SO + f".tmp{os.getpid()}"
+    subprocess.run([_nvcc(), "-shared", *NVCC_ARCH, "-o", tmp, *objs, "-lcudart"], check=True)
+    os.replace(tmp, LBM_SO)
+    return LBM_SO
+
+
+def build_all(force: bool = False) -> None:
+    build_geometry(force)
+    build_lbm(force)
