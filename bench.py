@@ -1,0 +1,402 @@
+"""Benchmark of the D3Q19-MRT permeability hot path on GB300.
+
+Workload (default): the 512^3 Boolean overlapping-sphere medium (radius 10
+voxels, SplitMix64 seed 1902_11193 + 1, porosity 0.40, periodic), Set B,
+tau = 1, body force 1e-6 along x, FP32 shifted populations.  One "step" is
+one time step of the production loop of lbm_run_to_convergence (fused
+stream-collide on every step, the fused mean-velocity reduction and stopping
+rule on the last two steps of every 100-step chunk).  Value = fluid-node
+updates per second (fluid MLUPS), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--layout sparse|aa|ab]
+  python bench.py --impl reference      # the FP64 CPU oracle, host cores
+
+Multi-GPU: one process per GPU, independent replicas of the same lattice
+(weak scaling); the lattice is not domain-decomposed, so ranks exchange
+nothing but the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {"fp32": 152, "fp16": 76, "fp64": 304}  # 19 reads + 19 writes
+SEED = 1902_11193 + 1
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=512)
+    p.add_argument("--layout", default="sparse", choices=["sparse", "aa", "ab"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
+    p.add_argument("--block-size", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the other-layout and permeability-error legs")
+    return p.parse_args()
+
+
+def workload(size):
+    from paper_1902_11193_gb300 import geometry
+
+    mask, nspheres = geometry.boolean(size, 10, 0.40, seed=SEED)
+    return mask, nspheres
+
+
+def workload_name(args):
+    return (f"boolean-{args.size}^3 r=10 porosity=0.40 seed={SEED}; D3Q19-MRT Set B tau=1 "
+            f"F=1e-6 x; {args.precision} shifted; {args.layout} layout")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[3 + k].lower() in ("active", "1")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        rank = int(os.environ["RANK"])
+        local = int(os.environ.get("LOCAL_RANK", rank))
+        import torch
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist, rank, ws, local
+    return None, 0, 1, 0
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(mask, seconds=12.0, nz=64):
+    """FP64 oracle on a z-slab of the workload (periodic in z), stepped until
+    `seconds` of host time have passed; returns (fluid MLUPS, threads, text)."""
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    slab = np.ascontiguousarray(mask[:nz])
+    O = oracle.Solver(slab, oracle.rates("B", 1.0), [1e-6, 0.0, 0.0])
+    nf = int((slab == 0).sum())
+    O.step(1)  # first touch
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        O.step(1)
+        steps += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or steps >= 50:
+            break
+    mlups = nf * steps / dt / 1e6
+    text = (f"FP64 oracle, z-slab {mask.shape[2]}x{mask.shape[1]}x{nz} of the workload "
+            f"(periodic in z), {steps} steps in {dt:.1f} s")
+    return mlups, oracle.get_threads(), text
+
+
+def run_reference(args):
+    dist, rank, ws, _ = (None, 0, 1, 0)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    mask, _ = workload(args.size)
+    # each step is a bounded sample: one oracle step on a 512 x 512 x 8 slab
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    slab = np.ascontiguousarray(mask[:8])
+    nf = int((slab == 0).sum())
+    O = oracle.Solver(slab, oracle.rates("B", 1.0), [1e-6, 0.0, 0.0])
+    for _ in range(max(args.warmup, 0)):
+        O.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(1)
+    dt = time.perf_counter() - t0
+    mlups = nf * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "fluid MLUPS", "value": mlups, "unit": "fluid MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args),
+                   "sample": f"each step: one FP64 oracle step on the {args.size}x{args.size}x8 "
+                             "z-slab of the workload (periodic in z)"},
+        "cpu_baseline": {"value": mlups, "unit": "fluid MLUPS", "cores": oracle.get_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.size}x{args.size}x8 z-slab, {args.steps} steps"},
+        "e2e": {"value": mlups, "unit": "fluid MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+
+def make_solver(mask, args, layout=None, precision=None, stream=None, max_steps=1_000_000):
+    from paper_1902_11193_gb300 import lbm
+
+    return lbm.LBMSolver(mask, "B", 1.0, force=(1e-6, 0.0, 0.0),
+                         precision=precision or args.precision, layout=layout or args.layout,
+                         check_interval=100, max_steps=max_steps, stream=stream,
+                         block_size=args.block_size)
+
+
+def time_production_loop(S, steps, stream):
+    """Events around lbm_run_to_convergence(tol=0) capped at `steps`."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rc, taken = S.run_to_convergence(0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert taken == steps, (rc, taken)
+    return e0.elapsed_time(e1)
+
+
+def time_kernel_launches(S, n, stream):
+    """Average device time of one plain stream-collide launch (events between
+    consecutive launches on the launching stream)."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(n):
+        S.step(1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    d = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+    return float(np.mean(d)), float(np.min(d))
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1902_11193_gb300 import lbm
+
+    dist, rank, ws, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    mask, nspheres = workload(args.size)
+    nf = int((mask == 0).sum())
+    N = mask.size
+    warm = max(args.warmup, 3)
+
+    S = make_solver(mask, args, stream=stream, max_steps=args.steps)
+    l0 = S.kernel_launches
+    S.step(warm)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches0 = S.kernel_launches
+    with ClockSampler(local) as clk:
+        ms = time_production_loop(S, args.steps, stream)
+    launches = S.kernel_launches - launches0
+    k_fp = S.permeability()
+    ms = max_over_ranks(dist, ms)
+    value = nf * args.steps * ws / (ms * 1e-3) / 1e6
+    # the dominant kernel alone: per-launch event timing on its stream
+    kmean, kmin = time_kernel_launches(S, 50, stream)
+    S.close()
+    del S
+
+    peak, peak_kind = load_peaks()
+    bpu = BYTES_PER_UPDATE[args.precision]
+    achieved = bpu * nf / (kmean * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.layout}_{args.precision}.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as fh:
+                traffic = json.load(fh).get("bytes_per_launch_512")
+        except Exception:
+            traffic = None
+
+    out = {
+        "metric": "fluid MLUPS", "value": value, "unit": "fluid MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f32 (f16 storage)", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "nodes": N, "fluid_nodes": nf,
+                   "spheres": nspheres, "l2": "inputs larger than L2 "
+                   f"({bpu // 2 * (nf if args.layout == 'sparse' else N) / 1e9:.1f} GB of "
+                   "populations), no flush", "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"stream-collide {args.layout} {args.precision}",
+                     "algorithmic_bytes_per_launch": bpu * nf,
+                     "launch_ms_mean": kmean, "launch_ms_min": kmin,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "permeability_lu": float(k_fp[0]),
+    }
+
+    if rank == 0 and not args.no_extra:
+        out["layouts"] = {}
+        for lay in ("aa", "sparse", "ab"):
+            if lay == args.layout:
+                continue
+            S2 = make_solver(mask, args, layout=lay, stream=stream, max_steps=200)
+            S2.step(warm)
+            m2 = time_production_loop(S2, 200, stream)
+            out["layouts"][lay] = nf * 200 / (m2 * 1e-3) / 1e6
+            S2.close()
+        out["perm_rel_err"] = permeability_errors(args, stream)
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_run(mask, args, stream)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, text = oracle_sample(mask)
+        out["cpu_baseline"] = {"value": v, "unit": "fluid MLUPS", "cores": cores,
+                               "kind": "oracle", "sample": text}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def permeability_errors(args, stream):
+    """Permeability of the 32^3 simple-cubic cell (sphere r = 12, Set E(3/16),
+    tau = 1, F = 1e-6) at the FP64 oracle's stop step, per precision, against
+    the stored oracle value (tests/golden/oracle_config1.txt)."""
+    from paper_1902_11193_gb300 import geometry, lbm
+
+    path = os.path.join(ROOT, "tests", "golden", "oracle_config1.txt")
+    row = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")][0]
+    steps, k_ora = int(row[0]), float(row[1])
+    mask = geometry.sphere_array(32, "sc", r=12)
+    res = {"workload": "32^3 SC r=12, Set E(3/16), tau=1, F=1e-6, at the oracle's stop step "
+                       f"{steps} (tol 1e-9)", "k_oracle": k_ora}
+    for prec, lay in (("fp64", "ab"), ("fp32", "aa"), ("fp32", "sparse"), ("fp16", "sparse")):
+        S = lbm.LBMSolver(mask, "E", 1.0, 3 / 16, (1e-6, 0, 0), precision=prec, layout=lay,
+                          stream=stream)
+        S.step(steps)
+        k = S.permeability()[0]
+        res[f"{prec}_{lay}"] = abs(k - k_ora) / abs(k_ora)
+        S.close()
+    return res
+
+
+def e2e_run(mask, args, stream):
+    """The whole job through the C ABI from host memory: lbm_create from the
+    host mask (H2D), the production loop, lbm_permeability (D2H)."""
+    import torch
+
+    steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = make_solver(mask, args, stream=stream, max_steps=steps)
+    S.run_to_convergence(0.0)
+    k = S.permeability()
+    t1 = time.perf_counter()
+    S.close()
+    nf = int((mask == 0).sum())
+    chunks = (steps + 99) // 100
+    return {"value": nf * steps / (t1 - t0) / 1e6, "unit": "fluid MLUPS",
+            "h2d_bytes_per_step": mask.nbytes / steps,
+            "d2h_bytes_per_step": (chunks * (2 * 3 * 8 + 4) + 3 * 8) / steps,
+            "wall_s": t1 - t0, "permeability_lu": float(k[0]),
+            "includes": "lbm_create (mask upload, link tables, allocation), the production "
+                        "loop, lbm_permeability"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

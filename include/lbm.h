@@ -1,0 +1,173 @@
+/*
+ * lbm.h - C ABI of the GB300 D3Q19-MRT lattice Boltzmann permeability solver.
+ *
+ * Method: Rao & Schaefer, "Lattice Boltzmann Models for Micro-tomographic
+ * Pore-spaces" (arXiv:1902.11193).  Stokes flow through a binary voxel image
+ * is time-stepped with the D3Q19 MRT lattice Boltzmann equation with Guo
+ * forcing (eqs. MRT Collision, LBE-MRT, MRT-LBE, Guo_Forcing; Sec. 2.2.1),
+ * equilibrium moments of eq. (MRT Equi), relaxation rates of Table 2 (Sets
+ * A-E as functions of tau and the magic parameter Lambda, eq. Magic param),
+ * a uniform body force with periodic boundaries (Sec. 2.4), bounceback on the
+ * solid mask applied at the half-link, and the permeability of eq. (perm_calc)
+ * from the mean velocity, with the stopping rule of eq. (convergence).
+ *
+ * Conventions shared by every call:
+ *  - The voxel image ("mask") is uint8 [Lz][Ly][Lx], x fastest, 1 = solid,
+ *    0 = fluid.  dims = {Lx, Ly, Lz}.  Node index n = x + Lx*(y + Ly*z).
+ *  - D3Q19 velocity order: i = 0 rest; 1..6 = +x, -x, +y, -y, +z, -z;
+ *    7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
+ *    (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
+ *  - Populations exchanged through this ABI are unshifted f_i in FP64,
+ *    laid out [19][N], holding the post-collision state after the last step
+ *    (solid nodes hold the rest value w_i).  Internally they are stored as
+ *    shifted deviations f_i - w_i (rho0 = 1).
+ *  - Velocities are u = (sum_i c_i f_i + F/2) / rho0 of the streamed state
+ *    (the shifted velocity of Sec. 2.2.1), 0 at solid voxels.  Mean values are
+ *    over all N voxels (superficial velocity).
+ *  - Every pointer argument is a HOST pointer unless the name says _dev.
+ *    The caller owns all buffers it passes; the context owns its device memory.
+ *  - Return value 0 = success, a negative LBM_E* code on failure; a failed
+ *    call leaves the context usable unless it returned LBM_ECUDA.
+ *  - One context is used by one host thread at a time.  All device work runs
+ *    on the context's CUDA stream; calls that return host data synchronise it.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,      /* bad argument: tau <= 1/2, rate outside (0,2), dims, mask */
+    LBM_ENOMEM = -2,      /* device or host allocation failed */
+    LBM_ECUDA = -3,       /* CUDA runtime error (see lbm_last_cuda_error) */
+    LBM_ENOTCONV = -4,    /* max_steps reached before the stopping rule held */
+    LBM_EUNSTABLE = -5,   /* non-finite density or velocity detected */
+    LBM_ETIMEOUT = -6,    /* a bounded device wait expired */
+    LBM_ENOSTATE = -7,    /* operation needs a state the context does not have */
+    LBM_EIO = -8          /* checkpoint file could not be read or written */
+};
+
+/* Relaxation-rate sets of Table 2; SRT sets every rate to 1/tau. */
+typedef enum { LBM_SET_A = 0, LBM_SET_B, LBM_SET_C, LBM_SET_D, LBM_SET_E, LBM_SET_SRT } lbm_set;
+
+/* Storage precision of the populations.  FP64 stores and computes in double;
+ * FP32_SHIFTED stores f_i - w_i in float and computes in float;
+ * FP16_SHIFTED stores 2^S (f_i - w_i) in half and computes in float.  Mean
+ * velocities and residuals are always accumulated in double. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP16_SHIFTED = 2 } lbm_precision;
+
+/* AB: two population arrays, pull stream.  AA: one array, in-place AA
+ * pattern (even steps read and write a node's own slots swapped, odd steps
+ * read and write neighbour slots).  SPARSE: AA pattern over the list of fluid
+ * nodes with a neighbour table; solid voxels take no storage. */
+typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1, LBM_LAYOUT_SPARSE = 2 } lbm_layout;
+
+typedef struct {
+    int32_t precision;        /* lbm_precision, default LBM_FP32_SHIFTED */
+    int32_t layout;           /* lbm_layout, default LBM_LAYOUT_AA */
+    int32_t check_interval;   /* K: stopping rule evaluated every K steps, default 100 */
+    int32_t linear_eq;        /* 1: drop the quadratic equilibrium and forcing terms
+                                 (Stokes simplification, Sec. 2.2.1); default 0 */
+    int64_t max_steps;        /* lbm_run_to_convergence limit, default 1000000 */
+    void *cuda_stream;        /* cudaStream_t to run on; NULL: the context makes one */
+    int32_t fp16_scale_log2;  /* S for FP16 storage; 0 selects it from the drive */
+    int32_t block_size;       /* threads per block of the stream-collide kernel;
+                                 0 = default (256) */
+} lbm_options;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void lbm_default_options(lbm_options *opt);
+
+/* Relaxation rates s[19] (diagonal of S, eq. MRT params) of Table 2 for
+ * (set, tau, Lambda).  Lambda is used by Set E only.  Returns LBM_EINVAL for
+ * tau <= 1/2, Lambda <= 0 with Set E, or an unknown set. */
+int lbm_rates(int32_t set, double tau, double Lambda, double s[19]);
+
+/* Creates a solver for the voxel image `mask` (host, Lz*Ly*Lx bytes, copied;
+ * the caller keeps ownership).  force = body force density F = rho0 a
+ * (Sec. 2.4), applied at every fluid node.  opt may be NULL (defaults).
+ * The state starts at rest (f_i = w_i).  On success *out owns all device
+ * memory until lbm_destroy.  Errors: LBM_EINVAL (dims <= 0, N >= 2^31, mask
+ * entries other than 0/1, bad rates), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], int32_t set,
+               double tau, double Lambda, const double force[3], const lbm_options *opt);
+
+/* Like lbm_create, with the 19 relaxation rates given directly (s[0], s[3],
+ * s[5], s[7] must be 0; the others in (0, 2); s[9] = 1/tau sets the
+ * viscosity nu = (1/s[9] - 1/2)/3). */
+int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3],
+                     const double s[19], const double force[3], const lbm_options *opt);
+
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Advances n >= 0 time steps (eq. LBE with the MRT collision, pull stream,
+ * halfway bounceback).  Asynchronous on the context stream. */
+int lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Steps in chunks of check_interval until the stopping rule of eq.
+ * (convergence) holds: |U_b - U_a| <= tol |U_b| for the mean velocity along the
+ * drive (the largest |F_j|) measured in the last two steps of a chunk.
+ * *steps_taken (nullable) receives the steps run by this call.  Returns 0,
+ * LBM_ENOTCONV after max_steps (state kept), LBM_EUNSTABLE on non-finite
+ * values. */
+int lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t *steps_taken);
+
+/* Mean velocity U[3] of the current state after streaming (not advanced). */
+int lbm_mean_velocity(lbm_ctx *ctx, double U[3]);
+
+/* eq. (perm_calc) with body forcing: k_j = nu <u_j> / F_j, nu = (tau-1/2)/3,
+ * NaN where F_j == 0 (lattice units). */
+int lbm_permeability(lbm_ctx *ctx, double k[3]);
+
+/* Velocity field u[3][N] (host, caller buffer) of the streamed state. */
+int lbm_velocity(lbm_ctx *ctx, double *u);
+
+/* Post-collision populations f[19][N] (host, unshifted FP64) of the current
+ * state, and the inverse.  Sizes are 19*N doubles. */
+int lbm_get_populations(lbm_ctx *ctx, double *f);
+int lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* Post-collision populations at selected nodes: nodes[count] are node
+ * indices n = x + Lx*(y + Ly*z) (host); f[count][19] (host) receives the
+ * unshifted FP64 values of each node (w_i at solid nodes).  Sized for
+ * sampled checks of lattices too large to copy whole.  LBM_EINVAL for an
+ * index outside [0, N). */
+int lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t count, double *f);
+
+/* Fluid-node count and per-direction bounceback link counts (links[i] =
+ * number of fluid nodes x whose upstream neighbour x - c_i is solid). */
+int lbm_link_counts(lbm_ctx *ctx, int64_t *n_fluid, int64_t links[19]);
+
+/* Sparse layout only: copies the fluid list fluid_idx[Nf] (node indices),
+ * the pull-neighbour table nbr[18][Nf] (fluid index of x - c_i, -1 where
+ * solid; direction i at row i-1) and the bounceback bits bbmask[Nf] (bit i
+ * set iff x - c_i is solid).  Any pointer may be NULL. */
+int lbm_sparse_tables(lbm_ctx *ctx, int32_t *fluid_idx, int32_t *nbr, uint32_t *bbmask);
+
+/* Number of time steps taken since creation (or since the loaded checkpoint). */
+int64_t lbm_steps_done(const lbm_ctx *ctx);
+
+/* Checkpoint: writes dims, mask, rates, force, options, step count and the
+ * stored populations to a file; lbm_load recreates an identical context
+ * (same stream if opt is NULL: a fresh one).  Resuming continues bit-identically. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt);
+
+/* Number of CUDA kernels this context has launched (for launch accounting). */
+int64_t lbm_kernel_launches(const lbm_ctx *ctx);
+
+const char *lbm_strerror(int code);
+/* Text of the last CUDA runtime error seen by this library (thread-local). */
+const char *lbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

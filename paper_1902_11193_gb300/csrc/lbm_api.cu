@@ -1,0 +1,573 @@
+// C ABI of liblbm_gb300 (declared in include/lbm.h): context life cycle,
+// relaxation rates, time stepping, the stopping rule, permeability and the
+// state readers/writers.  All device work is queued on the context stream.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+int launch_step(lbm_ctx *c, bool reduce);
+int launch_velocity(lbm_ctx *c, double *u_dev, bool reduce);
+void launch_export(lbm_ctx *c, double *f_dev);
+void launch_import(lbm_ctx *c, const double *f_dev);
+void launch_export_at(lbm_ctx *c, const int64_t *nodes_dev, int count, double *f_dev);
+void launch_finalize(lbm_ctx *c, int nblk, double inv_total, double *out_dev);
+int build_dense_links(lbm_ctx *c, unsigned long long *d_links);
+int build_sparse_links(lbm_ctx *c, unsigned long long *d_links);
+
+static thread_local char g_cuda_err[256] = "";
+
+int launch_error(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return launch_error(e_); \
+    } while (0)
+
+extern "C" {
+
+void lbm_default_options(lbm_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = LBM_FP32_SHIFTED;
+    o->layout = LBM_LAYOUT_AA;
+    o->check_interval = 100;
+    o->linear_eq = 0;
+    o->max_steps = 1000000;
+    o->cuda_stream = nullptr;
+    o->fp16_scale_log2 = 0;
+    o->block_size = 0;
+}
+
+// Table 2 (Sec. 2.3); s_nu = 1/tau in every set.
+int lbm_rates(int32_t set, double tau, double Lambda, double s[19]) {
+    if (!s || !(tau > 0.5) || !isfinite(tau)) return LBM_EINVAL;
+    const double sn = 1.0 / tau;
+    const double k8 = 8.0 * (2.0 - sn) / (8.0 - sn);
+    double se, seps, sq, spi, sm;
+    switch (set) {
+    case LBM_SET_A: se = seps = sq = spi = sm = k8; break;
+    case LBM_SET_B: se = seps = spi = sn; sq = sm = k8; break;
+    case LBM_SET_C: se = 1.19; seps = 1.4; sq = 1.2; spi = 1.4; sm = 1.98; break;
+    case LBM_SET_D: se = seps = spi = sn; sq = k8; sm = 4.0 * (2.0 - sn) / (4.0 + sn); break;
+    case LBM_SET_E:
+        if (!(Lambda > 0.0) || !isfinite(Lambda)) return LBM_EINVAL;
+        se = seps = spi = sn;
+        sq = sm = 2.0 * (2.0 - sn) / (4.0 * Lambda * sn - sn + 2.0);
+        break;
+    case LBM_SET_SRT: se = seps = sq = spi = sm = sn; break;
+    default: return LBM_EINVAL;
+    }
+    const double t[19] = {0, se, seps, 0, sq, 0, sq, 0, sq, sn, spi, sn, spi, sn, sn, sn, sm, sm, sm};
+    memcpy(s, t, sizeof t);
+    return LBM_OK;
+}
+
+static int check_rates(const double s[19]) {
+    if (s[0] != 0.0 || s[3] != 0.0 || s[5] != 0.0 || s[7] != 0.0) return LBM_EINVAL;
+    for (int k : {1, 2, 4, 9, 10, 16})
+        if (!(s[k] > 0.0 && s[k] < 2.0)) return LBM_EINVAL;
+    // the kernels use one rate per moment group of eq. (MRT params)
+    if (s[6] != s[4] || s[8] != s[4] || s[11] != s[9] || s[13] != s[9] || s[14] != s[9] ||
+        s[15] != s[9] || s[12] != s[10] || s[17] != s[16] || s[18] != s[16])
+        return LBM_EINVAL;
+    return LBM_OK;
+}
+
+static void free_ctx(lbm_ctx *c) {
+    if (!c) return;
+    cudaFree(c->d_mask);
+    cudaFree(c->d_lw);
+    cudaFree(c->d_fidx);
+    cudaFree(c->d_nbr);
+    cudaFree(c->d_bb);
+    cudaFree(c->d_pop[0]);
+    cudaFree(c->d_pop[1]);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_U);
+    cudaFree(c->d_flag);
+    cudaFreeHost(c->h_U);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    free(c->h_mask);
+    delete c;
+}
+
+// FP16 storage scale 2^S: puts the expected population deviation, of order
+// the Stokes velocity |F| l^2 / (8 nu) for the mean pore chord l, near 2^12.
+static int auto_fp16_scale(const lbm_ctx *c) {
+    double Fm = fmax(fabs(c->F[0]), fmax(fabs(c->F[1]), fabs(c->F[2])));
+    if (Fm <= 0.0) return 20;
+    double faces = 0.0;
+    for (int i = 1; i <= 6; ++i) faces += (double)c->links[i];
+    const double phi = (double)c->Nf / (double)c->N;
+    const double Sv = fmax(faces / (double)c->N * (2.0 / 3.0), 1e-12);
+    double l = fmin(4.0 * phi / Sv, (double)fmax(c->Lx, fmax(c->Ly, c->Lz)));
+    const double nu = (c->tau - 0.5) / 3.0;
+    const double u = Fm * l * l / (8.0 * nu);
+    int S = (int)floor(log2(4096.0 / fmax(u, 1e-30)));
+    return S < 0 ? 0 : (S > 60 ? 60 : S);
+}
+
+int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], const double s[19],
+                     const double force[3], const lbm_options *opt) {
+    if (!out || !mask || !dims || !s || !force) return LBM_EINVAL;
+    *out = nullptr;
+    if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return LBM_EINVAL;
+    const int64_t N = (int64_t)dims[0] * dims[1] * dims[2];
+    if (N >= (int64_t(1) << 31)) return LBM_EINVAL;
+    if (check_rates(s) != LBM_OK) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(force[a])) return LBM_EINVAL;
+    lbm_options o;
+    lbm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.block_size == 0) o.block_size = 256;
+    if (o.block_size < 64 || o.block_size > 256 || (o.block_size & 31)) return LBM_EINVAL;
+    if (o.precision < LBM_FP64 || o.precision > LBM_FP16_SHIFTED) return LBM_EINVAL;
+    if (o.layout < LBM_LAYOUT_AB || o.layout > LBM_LAYOUT_SPARSE) return LBM_EINVAL;
+    if (o.check_interval < 1) o.check_interval = 1;
+    if (o.max_steps <= 0) o.max_steps = 1000000;
+    if (o.fp16_scale_log2 < 0 || o.fp16_scale_log2 > 60) return LBM_EINVAL;
+    int64_t Nf = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        if (mask[n] > 1) return LBM_EINVAL;
+        Nf += mask[n] == 0;
+    }
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    c->Lx = dims[0];
+    c->Ly = dims[1];
+    c->Lz = dims[2];
+    c->N = N;
+    c->Nf = Nf;
+    memcpy(c->s, s, sizeof c->s);
+    c->tau = 1.0 / s[9];
+    memcpy(c->F, force, sizeof c->F);
+    c->opt = o;
+    c->h_mask = (uint8_t *)malloc((size_t)N);
+    if (!c->h_mask) {
+        delete c;
+        return LBM_ENOMEM;
+    }
+    memcpy(c->h_mask, mask, (size_t)N);
+
+    int rc = LBM_OK;
+    auto fail = [&](int code) {
+        free_ctx(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return fail(launch_error(e));
+    if (o.cuda_stream) {
+        c->stream = (cudaStream_t)o.cuda_stream;
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(launch_error(e));
+        c->own_stream = true;
+    }
+#define CKF(call)                                       \
+    do {                                                \
+        cudaError_t e2 = (call);                        \
+        if (e2 != cudaSuccess) return fail(launch_error(e2)); \
+    } while (0)
+    CKF(cudaMalloc(&c->d_mask, (size_t)N));
+    CKF(cudaMemcpyAsync(c->d_mask, mask, (size_t)N, cudaMemcpyHostToDevice, c->stream));
+    unsigned long long *d_links = nullptr;
+    CKF(cudaMalloc(&d_links, sizeof(unsigned long long) * 19));
+    CKF(cudaMemsetAsync(d_links, 0, sizeof(unsigned long long) * 19, c->stream));
+    const bool sparse = o.layout == LBM_LAYOUT_SPARSE;
+    if (sparse) {
+        CKF(cudaMalloc(&c->d_fidx, sizeof(int32_t) * (size_t)(Nf > 0 ? Nf : 1)));
+        CKF(cudaMalloc(&c->d_nbr, sizeof(int32_t) * 18 * (size_t)(Nf > 0 ? Nf : 1)));
+        CKF(cudaMalloc(&c->d_bb, sizeof(uint32_t) * (size_t)(Nf > 0 ? Nf : 1)));
+        rc = build_sparse_links(c, d_links);
+    } else {
+        CKF(cudaMalloc(&c->d_lw, sizeof(uint32_t) * (size_t)N));
+        rc = build_dense_links(c, d_links);
+    }
+    if (rc != LBM_OK) {
+        cudaFree(d_links);
+        return fail(rc);
+    }
+    unsigned long long hl[19];
+    CKF(cudaMemcpyAsync(hl, d_links, sizeof hl, cudaMemcpyDeviceToHost, c->stream));
+    CKF(cudaStreamSynchronize(c->stream));
+    cudaFree(d_links);
+    for (int i = 0; i < 19; ++i) c->links[i] = (int64_t)hl[i];
+
+    const int64_t units = sparse ? Nf : N;
+    c->elem = o.precision == LBM_FP64 ? 8 : (o.precision == LBM_FP32_SHIFTED ? 4 : 2);
+    const size_t bytes = c->elem * 19 * (size_t)(units > 0 ? units : 1);
+    CKF(cudaMalloc(&c->d_pop[0], bytes));
+    CKF(cudaMemsetAsync(c->d_pop[0], 0, bytes, c->stream));  // g = f - w = 0: rest state
+    if (o.layout == LBM_LAYOUT_AB) {
+        CKF(cudaMalloc(&c->d_pop[1], bytes));
+        CKF(cudaMemsetAsync(c->d_pop[1], 0, bytes, c->stream));
+    }
+    // per-block partials for the largest grid a reducing launch can have
+    c->n_partial_blocks = (int)((N + 63) / 64);
+    CKF(cudaMalloc(&c->d_partials, sizeof(double) * 3 * (size_t)c->n_partial_blocks));
+    CKF(cudaMalloc(&c->d_U, sizeof(double) * 24));
+    CKF(cudaMalloc(&c->d_flag, sizeof(int)));
+    CKF(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    CKF(cudaMallocHost(&c->h_U, sizeof(double) * 26));
+    if (o.precision == LBM_FP16_SHIFTED) {
+        int S = o.fp16_scale_log2 ? o.fp16_scale_log2 : auto_fp16_scale(c);
+        c->opt.fp16_scale_log2 = S;
+        c->fp16_scale = ldexpf(1.0f, S);
+    } else {
+        c->fp16_scale = 0.0f;
+    }
+    CKF(cudaStreamSynchronize(c->stream));
+#undef CKF
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], int32_t set, double tau,
+               double Lambda, const double force[3], const lbm_options *opt) {
+    double s[19];
+    int rc = lbm_rates(set, tau, Lambda, s);
+    if (rc != LBM_OK) return rc;
+    return lbm_create_rates(out, mask, dims, s, force, opt);
+}
+
+void lbm_destroy(lbm_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+int lbm_step(lbm_ctx *c, int64_t n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    for (int64_t t = 0; t < n; ++t) launch_step(c, false);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// One measuring step: the mean streamed velocity lands in d_U[3*slot..].
+static int measured_step(lbm_ctx *c, int slot) {
+    int nblk = launch_step(c, true);
+    if (nblk > 0)
+        launch_finalize(c, nblk, 1.0 / (double)c->N, c->d_U + 3 * slot);
+    else
+        cudaMemsetAsync(c->d_U + 3 * slot, 0, 3 * sizeof(double), c->stream);
+    return LBM_OK;
+}
+
+static int read_U(lbm_ctx *c, int nslots) {
+    CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 3 * nslots, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync((int *)(c->h_U + 24), c->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
+    if (!c || !(tol >= 0.0)) return LBM_EINVAL;
+    int d = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
+    const int64_t K = c->opt.check_interval, maxs = c->opt.max_steps;
+    int64_t done = 0;
+    double Ua = NAN, Ub = NAN;
+    int rc = LBM_ENOTCONV;
+    while (done < maxs) {
+        int64_t chunk = K < maxs - done ? K : maxs - done;
+        int rr;
+        if (K >= 2 && chunk >= 2) {
+            for (int64_t t = 0; t < chunk - 2; ++t) launch_step(c, false);
+            measured_step(c, 0);
+            measured_step(c, 1);
+            CK(cudaGetLastError());
+            rr = read_U(c, 2);
+            if (rr) return rr;
+            Ua = c->h_U[d];
+            Ub = c->h_U[3 + d];
+        } else {
+            measured_step(c, 1);
+            CK(cudaGetLastError());
+            rr = read_U(c, 2);
+            if (rr) return rr;
+            Ua = Ub;
+            Ub = c->h_U[3 + d];
+        }
+        done += chunk;
+        const int flag = *(int *)(c->h_U + 24);
+        if (flag || !isfinite(c->h_U[3]) || !isfinite(c->h_U[4]) || !isfinite(c->h_U[5])) {
+            rc = LBM_EUNSTABLE;
+            break;
+        }
+        if (isfinite(Ua) && fabs(Ub - Ua) <= tol * fabs(Ub)) {
+            rc = LBM_OK;
+            break;
+        }
+    }
+    if (steps_taken) *steps_taken = done;
+    return rc;
+}
+
+int lbm_mean_velocity(lbm_ctx *c, double U[3]) {
+    if (!c || !U) return LBM_EINVAL;
+    int nblk = launch_velocity(c, nullptr, true);
+    if (nblk > 0)
+        launch_finalize(c, nblk, 1.0 / (double)c->N, c->d_U + 3 * 7);
+    else
+        CK(cudaMemsetAsync(c->d_U + 21, 0, 3 * sizeof(double), c->stream));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_U, c->d_U + 21, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int a = 0; a < 3; ++a) U[a] = c->h_U[a];
+    return LBM_OK;
+}
+
+int lbm_permeability(lbm_ctx *c, double k[3]) {
+    if (!c || !k) return LBM_EINVAL;
+    double U[3];
+    int rc = lbm_mean_velocity(c, U);
+    if (rc) return rc;
+    const double nu = (c->tau - 0.5) / 3.0;  // nu = c_s^2 (tau - 1/2)
+    for (int a = 0; a < 3; ++a) k[a] = c->F[a] != 0.0 ? nu * U[a] / c->F[a] : NAN;
+    return LBM_OK;
+}
+
+int lbm_velocity(lbm_ctx *c, double *u) {
+    if (!c || !u) return LBM_EINVAL;
+    double *d_u = nullptr;
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    CK(cudaMalloc(&d_u, bytes));
+    cudaError_t e = cudaMemsetAsync(d_u, 0, bytes, c->stream);
+    if (e == cudaSuccess) {
+        launch_velocity(c, d_u, false);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, d_u, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_u);
+    return launch_error(e);
+}
+
+int lbm_get_populations(lbm_ctx *c, double *f) {
+    if (!c || !f) return LBM_EINVAL;
+    double *d_f = nullptr;
+    const size_t bytes = sizeof(double) * 19 * (size_t)c->N;
+    CK(cudaMalloc(&d_f, bytes));
+    launch_export(c, d_f);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d_f, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_f);
+    if (e != cudaSuccess) return launch_error(e);
+    for (int64_t n = 0; n < c->N; ++n)
+        if (c->h_mask[n])
+            for (int i = 0; i < 19; ++i) f[(size_t)i * c->N + n] = weight(i);
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx *c, const double *f) {
+    if (!c || !f) return LBM_EINVAL;
+    double *d_f = nullptr;
+    const size_t bytes = sizeof(double) * 19 * (size_t)c->N;
+    CK(cudaMalloc(&d_f, bytes));
+    cudaError_t e = cudaMemcpyAsync(d_f, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        launch_import(c, d_f);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_f);
+    return launch_error(e);
+}
+
+int lbm_get_populations_at(lbm_ctx *c, const int64_t *nodes, int64_t count, double *f) {
+    if (!c || count < 0 || (count > 0 && (!nodes || !f)) || count > (int64_t(1) << 30))
+        return LBM_EINVAL;
+    for (int64_t k = 0; k < count; ++k)
+        if (nodes[k] < 0 || nodes[k] >= c->N) return LBM_EINVAL;
+    if (count == 0) return LBM_OK;
+    int64_t *d_nodes = nullptr;
+    CK(cudaMalloc(&d_nodes, sizeof(int64_t) * (size_t)count + sizeof(double) * 19 * (size_t)count));
+    double *d_f = (double *)(d_nodes + count);
+    cudaError_t e = cudaMemcpyAsync(d_nodes, nodes, sizeof(int64_t) * (size_t)count,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        launch_export_at(c, d_nodes, (int)count, d_f);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, d_f, sizeof(double) * 19 * (size_t)count, cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_nodes);
+    return launch_error(e);
+}
+
+int lbm_link_counts(lbm_ctx *c, int64_t *n_fluid, int64_t links[19]) {
+    if (!c) return LBM_EINVAL;
+    if (n_fluid) *n_fluid = c->Nf;
+    if (links) memcpy(links, c->links, sizeof c->links);
+    return LBM_OK;
+}
+
+int lbm_sparse_tables(lbm_ctx *c, int32_t *fidx, int32_t *nbr, uint32_t *bb) {
+    if (!c) return LBM_EINVAL;
+    if (c->opt.layout != LBM_LAYOUT_SPARSE) return LBM_ENOSTATE;
+    const size_t Nf = (size_t)c->Nf;
+    if (Nf == 0) return LBM_OK;
+    if (fidx) CK(cudaMemcpyAsync(fidx, c->d_fidx, 4 * Nf, cudaMemcpyDeviceToHost, c->stream));
+    if (nbr) CK(cudaMemcpyAsync(nbr, c->d_nbr, 4 * 18 * Nf, cudaMemcpyDeviceToHost, c->stream));
+    if (bb) CK(cudaMemcpyAsync(bb, c->d_bb, 4 * Nf, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_ctx *c) { return c ? c->steps : -1; }
+int64_t lbm_kernel_launches(const lbm_ctx *c) { return c ? c->launches : -1; }
+
+// ------------------------------------------------------------ checkpoints
+
+static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version;
+    int32_t dims[3];
+    double s[19];
+    double F[3];
+    int32_t precision, layout, check_interval, linear_eq, fp16_scale_log2, block_size;
+    int64_t max_steps;
+    int64_t steps;
+    int32_t cur;
+    int32_t pad;
+};
+
+int lbm_save(lbm_ctx *c, const char *path) {
+    if (!c || !path) return LBM_EINVAL;
+    const int64_t units = c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+    const size_t bytes = c->elem * 19 * (size_t)units;
+    std::vector<unsigned char> buf(bytes);
+    if (bytes) {
+        CK(cudaMemcpyAsync(buf.data(), c->opt.layout == LBM_LAYOUT_AB ? c->d_pop[c->cur] : c->d_pop[0],
+                           bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.dims[0] = c->Lx;
+    h.dims[1] = c->Ly;
+    h.dims[2] = c->Lz;
+    memcpy(h.s, c->s, sizeof h.s);
+    memcpy(h.F, c->F, sizeof h.F);
+    h.precision = c->opt.precision;
+    h.layout = c->opt.layout;
+    h.check_interval = c->opt.check_interval;
+    h.linear_eq = c->opt.linear_eq;
+    h.fp16_scale_log2 = c->opt.fp16_scale_log2;
+    h.block_size = c->opt.block_size;
+    h.max_steps = c->opt.max_steps;
+    h.steps = c->steps;
+    h.cur = 0;
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return LBM_EIO;
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(c->h_mask, 1, (size_t)c->N, fp) == (size_t)c->N &&
+              (bytes == 0 || fwrite(buf.data(), 1, bytes, fp) == bytes);
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : LBM_EIO;
+}
+
+int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
+    if (!out || !path) return LBM_EINVAL;
+    *out = nullptr;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return LBM_EIO;
+    CkptHeader h;
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    const int64_t N = (int64_t)h.dims[0] * h.dims[1] * h.dims[2];
+    if (h.dims[0] <= 0 || h.dims[1] <= 0 || h.dims[2] <= 0 || N >= (int64_t(1) << 31)) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    std::vector<uint8_t> mask((size_t)N);
+    if (fread(mask.data(), 1, (size_t)N, fp) != (size_t)N) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    lbm_options o;
+    lbm_default_options(&o);
+    if (opt) o.cuda_stream = opt->cuda_stream;
+    o.precision = h.precision;
+    o.layout = h.layout;
+    o.check_interval = h.check_interval;
+    o.linear_eq = h.linear_eq;
+    o.fp16_scale_log2 = h.fp16_scale_log2;
+    o.block_size = h.block_size;
+    o.max_steps = h.max_steps;
+    lbm_ctx *c = nullptr;
+    int rc = lbm_create_rates(&c, mask.data(), h.dims, h.s, h.F, &o);
+    if (rc != LBM_OK) {
+        fclose(fp);
+        return rc;
+    }
+    const int64_t units = c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+    const size_t bytes = c->elem * 19 * (size_t)units;
+    std::vector<unsigned char> buf(bytes);
+    bool ok = bytes == 0 || fread(buf.data(), 1, bytes, fp) == bytes;
+    fclose(fp);
+    if (!ok) {
+        lbm_destroy(c);
+        return LBM_EIO;
+    }
+    if (bytes) {
+        cudaError_t e = cudaMemcpyAsync(c->d_pop[0], buf.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            lbm_destroy(c);
+            return launch_error(e);
+        }
+    }
+    c->cur = 0;
+    c->steps = h.steps;
+    *out = c;
+    return LBM_OK;
+}
+
+const char *lbm_strerror(int code) {
+    switch (code) {
+    case LBM_OK: return "success";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA runtime error";
+    case LBM_ENOTCONV: return "not converged within max_steps";
+    case LBM_EUNSTABLE: return "non-finite density or velocity";
+    case LBM_ETIMEOUT: return "bounded device wait expired";
+    case LBM_ENOSTATE: return "operation not available in this state or layout";
+    case LBM_EIO: return "checkpoint I/O error";
+    default: return "unknown error";
+    }
+}
+
+const char *lbm_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

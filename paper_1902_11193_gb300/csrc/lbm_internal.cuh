@@ -1,0 +1,124 @@
+// Internal definitions shared by the CUDA translation units of liblbm_gb300.
+// D3Q19 lattice constants, kernel parameter blocks, storage traits and the
+// context structure behind the opaque lbm_ctx of include/lbm.h.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities: rest, six axis links (+ before -), twelve edge links in
+// opposite pairs.  The opposite of i is i+1 for odd i, i-1 for even i > 0.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)
+               ? 1
+               : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)
+               ? 1
+               : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)
+               ? 1
+               : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+__host__ __device__ constexpr double weight(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Bit 31 of a dense link word marks a solid voxel; bit i (1..18) marks a
+// bounceback link: the upstream neighbour x - c_i is solid.
+constexpr uint32_t SOLID_BIT = 1u << 31;
+
+// Relaxation rates and drive in the arithmetic type of the kernel.
+template <typename T>
+struct Collide {
+    T se, seps, sq, snu, spi, sm;  // diag(S) of eq. (MRT params), grouped
+    T Fx, Fy, Fz;                  // body force density
+    int linear;                    // drop quadratic equilibrium / forcing terms
+};
+
+struct Dims {
+    int Lx, Ly, Lz;
+    uint32_t N;  // Lx*Ly*Lz < 2^31
+};
+
+// Storage traits: S is the stored type, C the arithmetic type.
+template <typename S>
+struct Store;
+template <>
+struct Store<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const double *p, float) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v, float) { *p = v; }
+};
+template <>
+struct Store<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    using C = float;
+    // stored value h = 2^S (f - w); `scale` carries 2^S on store, 2^-S on load
+    static __device__ __forceinline__ float ld(const __half *p, float inv) {
+        return __half2float(*p) * inv;
+    }
+    static __device__ __forceinline__ void st(__half *p, float v, float sc) {
+        *p = __float2half_rn(v * sc);
+    }
+};
+
+// Per-launch reduction target: per-block partial sums of (ux, uy, uz) in
+// double, and a device flag raised on non-finite density or momentum.
+struct Reduce {
+    double *partials;  // [gridDim.x][3], or nullptr for no reduction
+    int *flag;
+};
+
+int launch_error(cudaError_t e);
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    int Lx, Ly, Lz;
+    int64_t N, Nf;
+    double s[19];
+    double tau;  // 1/s_nu
+    double F[3];
+    lbm_options opt;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+
+    uint8_t *d_mask;      // [N]
+    uint32_t *d_lw;       // [N] dense link words (AB, AA)
+    int32_t *d_fidx;      // [Nf] sparse: node index of each fluid node
+    int32_t *d_nbr;       // [18][Nf] sparse: fluid index of x - c_i, -1 if solid
+    uint32_t *d_bb;       // [Nf] sparse: bounceback bits
+    void *d_pop[2];       // populations; AB uses both, AA and SPARSE one
+    size_t elem;          // bytes per stored population value
+    float fp16_scale;     // 2^S (FP16 storage)
+    int cur;              // AB: index of the array holding the current state
+    int64_t steps;        // time steps taken
+    int64_t links[19];
+
+    double *d_partials;   // [max blocks][3]
+    int n_partial_blocks;
+    double *d_U;          // [8][3]: reduced mean velocities
+    int *d_flag;          // non-finite flag
+    double *h_U;          // pinned [8*3 + 2]
+    int64_t launches;
+    uint8_t *h_mask;      // host copy of the mask [N]
+};

@@ -1,0 +1,531 @@
+// Stream-collide kernels of the D3Q19-MRT solver and the kernels that read
+// or write its state.
+//
+// One thread updates one fluid node per launch: it gathers the 19 streamed
+// populations (pull scheme, eq. LBE; halfway bounceback where the upstream
+// voxel is solid), runs the MRT collision with Guo forcing in registers
+// (lbm_collide.cuh), stores the 19 post-collision populations, and, on
+// launches that measure, adds its shifted velocity to a per-block FP64
+// partial sum.  Populations are structure-of-arrays, slot i of node n at
+// i*N + n (N = nodes, or fluid nodes for the sparse layout), so each warp's
+// access to a slot is one contiguous run.
+//
+// Layouts
+//  AB      pull from array `src` into array `dst` (two arrays).
+//  AA      one array.  An even step reads a node's own slots and writes the
+//          post-collision value of direction opp(j) back into slot j; an odd
+//          step reads slot opp(j) of the upstream neighbour x - c_j (slot j of
+//          the node itself if that neighbour is solid) and writes the
+//          post-collision value of direction opp(j) back to the same place.
+//          Each thread therefore reads and writes exactly the same 19
+//          locations, so no two threads touch one location within a step.
+//  SPARSE  the AA pattern over the fluid list, neighbours from a table.
+#include <math.h>
+
+#include "lbm_collide.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- helpers
+
+struct DenseNode {
+    int x, xm, xp;
+    uint32_t row[3][3];  // Lx*(y' + Ly*z') for y' in {y-1, y, y+1}, z' likewise (wrapped)
+
+    __device__ __forceinline__ void init(uint32_t n, const Dims &d) {
+        uint32_t t = n / (uint32_t)d.Lx;
+        x = (int)(n - t * (uint32_t)d.Lx);
+        int z = (int)(t / (uint32_t)d.Ly);
+        int y = (int)(t - (uint32_t)z * (uint32_t)d.Ly);
+        xm = x == 0 ? d.Lx - 1 : x - 1;
+        xp = x == d.Lx - 1 ? 0 : x + 1;
+        int ys[3] = {y == 0 ? d.Ly - 1 : y - 1, y, y == d.Ly - 1 ? 0 : y + 1};
+        int zs[3] = {z == 0 ? d.Lz - 1 : z - 1, z, z == d.Lz - 1 ? 0 : z + 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                row[a][b] = (uint32_t)d.Lx * ((uint32_t)ys[a] + (uint32_t)d.Ly * (uint32_t)zs[b]);
+    }
+    // node index of the upstream neighbour x - c_j
+    __device__ __forceinline__ uint32_t up(int j) const {
+        int xs = cx(j) > 0 ? xm : (cx(j) < 0 ? xp : x);
+        return (uint32_t)xs + row[1 - cy(j)][1 - cz(j)];
+    }
+};
+
+template <typename C>
+__device__ __forceinline__ void block_reduce_velocity(C jx, C jy, C jz, bool fluid,
+                                                      const Reduce &red) {
+    double v[3] = {fluid ? (double)jx : 0.0, fluid ? (double)jy : 0.0, fluid ? (double)jz : 0.0};
+    if (fluid && !isfinite(v[0] + v[1] + v[2])) atomicOr(red.flag, 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+    __shared__ double sm[32][3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm[wid][0] = v[0];
+        sm[wid][1] = v[1];
+        sm[wid][2] = v[2];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double acc = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) acc += sm[w][threadIdx.x];
+        red.partials[3 * (size_t)blockIdx.x + threadIdx.x] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- AB pull
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__restrict__ dst,
+                                            const uint32_t *__restrict__ lw, Dims d,
+                                            Collide<typename Store<S>::C> p, float ld_scale,
+                                            float st_scale, Reduce red) {
+    using C = typename Store<S>::C;
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
+    const bool fluid = !(w & SOLID_BIT);
+    C jx = C(0), jy = C(0), jz = C(0);
+    if (fluid) {
+        DenseNode nd;
+        nd.init(n, d);
+        C g[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            if (j == 0)
+                g[j] = Store<S>::ld(src + n, ld_scale);
+            else if (w & (1u << j))
+                g[j] = Store<S>::ld(src + (size_t)opp(j) * d.N + n, ld_scale);
+            else
+                g[j] = Store<S>::ld(src + (size_t)j * d.N + nd.up(j), ld_scale);
+        }
+        mrt_collide<C>(g, p, jx, jy, jz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], st_scale);
+    }
+    if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
+}
+
+// ------------------------------------------------------ AA, dense and sparse
+
+// Location (flat offset) of logical direction j for node n: the even pattern
+// is slot j of the node; the odd pattern is slot opp(j) of the upstream
+// neighbour, or slot j of the node when that neighbour is solid.
+template <bool ODD>
+__device__ __forceinline__ size_t aa_loc_dense(int j, uint32_t n, uint32_t w,
+                                               const DenseNode &nd, uint32_t N) {
+    if (!ODD || j == 0 || (w & (1u << j))) return (size_t)j * N + n;
+    return (size_t)opp(j) * N + nd.up(j);
+}
+
+template <typename S, bool ODD>
+__global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ lw, Dims d,
+                                            Collide<typename Store<S>::C> p, float ld_scale,
+                                            float st_scale, Reduce red) {
+    using C = typename Store<S>::C;
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
+    const bool fluid = !(w & SOLID_BIT);
+    C jx = C(0), jy = C(0), jz = C(0);
+    if (fluid) {
+        DenseNode nd;
+        if (ODD) nd.init(n, d);
+        C g[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) g[j] = Store<S>::ld(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), ld_scale);
+        mrt_collide<C>(g, p, jx, jy, jz);
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            Store<S>::st(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), g[opp(j)], st_scale);
+    }
+    if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
+}
+
+template <typename S, bool ODD>
+__global__ void __launch_bounds__(256) k_sparse(S *A, const int32_t *__restrict__ nbr,
+                                                const uint32_t *__restrict__ bb, uint32_t Nf,
+                                                Collide<typename Store<S>::C> p, float ld_scale,
+                                                float st_scale, Reduce red) {
+    using C = typename Store<S>::C;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool fluid = k < Nf;
+    C jx = C(0), jy = C(0), jz = C(0);
+    if (fluid) {
+        size_t loc[Q];
+        if (ODD) {
+            const uint32_t bits = bb[k];
+            loc[0] = k;
+#pragma unroll
+            for (int j = 1; j < Q; ++j)
+                loc[j] = (bits & (1u << j))
+                             ? (size_t)j * Nf + k
+                             : (size_t)opp(j) * Nf + (uint32_t)nbr[(size_t)(j - 1) * Nf + k];
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) loc[j] = (size_t)j * Nf + k;
+        }
+        C g[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) g[j] = Store<S>::ld(A + loc[j], ld_scale);
+        mrt_collide<C>(g, p, jx, jy, jz);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) Store<S>::st(A + loc[j], g[opp(j)], st_scale);
+    }
+    if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
+}
+
+// ------------------------------------------------------- reduction finalise
+
+// Fixed-order sum of the per-block partials: thread t adds blocks t, t+T, ...
+// in order, then a fixed shared-memory tree.  out[a] = sum / N_total.
+__global__ void __launch_bounds__(1024) k_finalize(const double *__restrict__ partials, int nblk,
+                                                   double inv_total, double *out) {
+    __shared__ double sm[3][1024];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] += partials[3 * (size_t)b + a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] = acc[a];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] += sm[a][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = sm[threadIdx.x][0] * inv_total;
+}
+
+// ------------------------------------------------ state readers and writers
+
+// Where the current state keeps, for unit u (node or fluid index), the
+// streamed population of direction j (kind 0) or the post-collision
+// population of direction opp(j) (kind 1).
+struct StateView {
+    int layout;      // LBM_LAYOUT_*
+    int parity;      // steps % 2 (AA, SPARSE)
+    uint32_t units;  // N (dense) or Nf (sparse)
+    const uint32_t *lw;
+    const int32_t *nbr;
+    const uint32_t *bb;
+    Dims d;
+};
+
+// Returns the flat offset for unit u, direction j.  For AB, kind 0 reads the
+// pull location in the current array and kind 1 the node's own slot
+// (holding f*_opp(j) for slot opp(j)).
+__device__ __forceinline__ size_t state_loc(const StateView &v, uint32_t u, int j, int kind,
+                                            uint32_t w, const DenseNode &nd) {
+    if (v.layout == LBM_LAYOUT_AB) {
+        if (kind == 1) return (size_t)opp(j) * v.units + u;  // f*_opp(j) lives in slot opp(j)
+        if (j == 0) return u;
+        if (w & (1u << j)) return (size_t)opp(j) * v.units + u;
+        return (size_t)j * v.units + nd.up(j);
+    }
+    // AA / SPARSE: streamed state sits at the parity's pattern, the
+    // post-collision state (direction opp(j) at location j) at the other one.
+    const bool odd = (kind == 0) ? (v.parity == 1) : (v.parity == 0);
+    if (!odd || j == 0 || (w & (1u << j))) return (size_t)j * v.units + u;
+    if (v.layout == LBM_LAYOUT_AA) return (size_t)opp(j) * v.units + nd.up(j);
+    return (size_t)opp(j) * v.units + (uint32_t)v.nbr[(size_t)(j - 1) * v.units + u];
+}
+
+__device__ __forceinline__ bool state_unit(const StateView &v, uint32_t u, uint32_t &node,
+                                           uint32_t &w, DenseNode &nd) {
+    if (v.layout == LBM_LAYOUT_SPARSE) {
+        w = v.bb[u];
+        node = u;
+        return true;
+    }
+    w = v.lw[u];
+    node = u;
+    if (w & SOLID_BIT) return false;
+    nd.init(u, v.d);
+    return true;
+}
+
+// Streamed-state velocity u = sum c f + F/2 per unit; writes the field
+// (dense node order, indexed through fidx for the sparse layout) and/or
+// block partials for the mean.
+template <typename S>
+__global__ void __launch_bounds__(256) k_velocity(const S *A, StateView v,
+                                                  const int32_t *__restrict__ fidx, double Fx,
+                                                  double Fy, double Fz, float ld_scale,
+                                                  double *u_out, Reduce red) {
+    using C = typename Store<S>::C;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    bool fluid = false;
+    double jx = 0.0, jy = 0.0, jz = 0.0;
+    if (u < v.units) {
+        uint32_t node, w;
+        DenseNode nd;
+        fluid = state_unit(v, u, node, w, nd);
+        if (fluid) {
+#pragma unroll
+            for (int j = 1; j < Q; ++j) {
+                double gj = (double)Store<S>::ld(A + state_loc(v, u, j, 0, w, nd), ld_scale);
+                jx += cx(j) * gj;
+                jy += cy(j) * gj;
+                jz += cz(j) * gj;
+            }
+            jx += 0.5 * Fx;
+            jy += 0.5 * Fy;
+            jz += 0.5 * Fz;
+        }
+        if (u_out) {
+            size_t N = v.d.N;
+            size_t out = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
+            u_out[out] = jx;
+            u_out[N + out] = jy;
+            u_out[2 * N + out] = jz;
+        }
+    }
+    if (red.partials) block_reduce_velocity<double>(jx, jy, jz, fluid, red);
+}
+
+// Export of the post-collision state as unshifted FP64 f[19][N] (dense node
+// order).  Solid nodes are left to the caller (who fills w_i).
+template <typename S>
+__global__ void __launch_bounds__(256) k_export(const S *A, StateView v,
+                                                const int32_t *__restrict__ fidx, float ld_scale,
+                                                double *f) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= v.units) return;
+    uint32_t node, w;
+    DenseNode nd;
+    if (!state_unit(v, u, node, w, nd)) return;
+    const size_t out = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        double gv = (double)Store<S>::ld(A + state_loc(v, u, j, 1, w, nd), ld_scale);
+        f[(size_t)opp(j) * v.d.N + out] = gv + weight(opp(j));
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_import(S *A, StateView v, const int32_t *__restrict__ fidx,
+                                                float st_scale, const double *f) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= v.units) return;
+    uint32_t node, w;
+    DenseNode nd;
+    if (!state_unit(v, u, node, w, nd)) return;
+    const size_t in = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        double fv = f[(size_t)opp(j) * v.d.N + in] - weight(opp(j));
+        Store<S>::st(A + state_loc(v, u, j, 1, w, nd), (typename Store<S>::C)fv, st_scale);
+    }
+}
+
+// Post-collision populations at listed node indices, f[k][19] unshifted.
+// Sparse layouts find the fluid index by binary search in the sorted list.
+template <typename S>
+__global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
+                                                   const int32_t *__restrict__ fidx,
+                                                   const int64_t *__restrict__ nodes, int count,
+                                                   float ld_scale, double *f) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t node = (uint32_t)nodes[k];
+    uint32_t unit = node;
+    bool fluid;
+    uint32_t w = 0;
+    DenseNode nd;
+    if (v.layout == LBM_LAYOUT_SPARSE) {
+        int lo = 0, hi = (int)v.units - 1;
+        fluid = false;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t m = (uint32_t)fidx[mid];
+            if (m == node) {
+                fluid = true;
+                unit = (uint32_t)mid;
+                break;
+            }
+            if (m < node) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        if (fluid) w = v.bb[unit];
+    } else {
+        w = v.lw[node];
+        fluid = !(w & SOLID_BIT);
+        if (fluid) nd.init(node, v.d);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        double val = weight(opp(j));
+        if (fluid) val += (double)Store<S>::ld(A + state_loc(v, unit, j, 1, w, nd), ld_scale);
+        f[(size_t)k * Q + opp(j)] = val;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline unsigned nblocks(uint64_t units, int bs) { return (unsigned)((units + bs - 1) / bs); }
+
+template <typename S>
+int launch_step_t(lbm_ctx *c, bool reduce) {
+    using Cm = typename Store<S>::C;
+    Collide<Cm> p;
+    p.se = (Cm)c->s[1];
+    p.seps = (Cm)c->s[2];
+    p.sq = (Cm)c->s[4];
+    p.snu = (Cm)c->s[9];
+    p.spi = (Cm)c->s[10];
+    p.sm = (Cm)c->s[16];
+    p.Fx = (Cm)c->F[0];
+    p.Fy = (Cm)c->F[1];
+    p.Fz = (Cm)c->F[2];
+    p.linear = c->opt.linear_eq;
+    const int bs = c->opt.block_size;
+    const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    const float sts = c->fp16_scale > 0.f ? c->fp16_scale : 1.0f;
+    Dims d{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
+    Reduce red{reduce ? c->d_partials : nullptr, c->d_flag};
+    const bool odd = (c->steps & 1) != 0;
+    unsigned grid;
+    switch (c->opt.layout) {
+    case LBM_LAYOUT_AB:
+        grid = nblocks(c->N, bs);
+        k_ab<S><<<grid, bs, 0, c->stream>>>((const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur],
+                                            c->d_lw, d, p, lds, sts, red);
+        c->cur = 1 - c->cur;
+        break;
+    case LBM_LAYOUT_AA:
+        grid = nblocks(c->N, bs);
+        if (odd)
+            k_aa<S, true><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
+        else
+            k_aa<S, false><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
+        break;
+    default:
+        grid = nblocks(c->Nf, bs);
+        if (grid == 0) break;
+        if (odd)
+            k_sparse<S, true><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_nbr, c->d_bb,
+                                                          (uint32_t)c->Nf, p, lds, sts, red);
+        else
+            k_sparse<S, false><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_nbr, c->d_bb,
+                                                           (uint32_t)c->Nf, p, lds, sts, red);
+        break;
+    }
+    c->launches++;
+    c->steps++;
+    if (reduce) return (int)grid;
+    return 0;
+}
+
+static StateView make_view(const lbm_ctx *c) {
+    StateView v;
+    v.layout = c->opt.layout;
+    v.parity = (int)(c->steps & 1);
+    v.units = (uint32_t)(c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N);
+    v.lw = c->d_lw;
+    v.nbr = c->d_nbr;
+    v.bb = c->d_bb;
+    v.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
+    return v;
+}
+
+static const void *cur_pop(const lbm_ctx *c) {
+    return c->opt.layout == LBM_LAYOUT_AB ? c->d_pop[c->cur] : c->d_pop[0];
+}
+
+template <typename S>
+int launch_velocity_t(lbm_ctx *c, double *u_dev, bool reduce) {
+    StateView v = make_view(c);
+    const int bs = 256;
+    const unsigned grid = nblocks(v.units, bs);
+    if (grid == 0) return 0;
+    Reduce red{reduce ? c->d_partials : nullptr, c->d_flag};
+    const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    k_velocity<S><<<grid, bs, 0, c->stream>>>((const S *)cur_pop(c), v, c->d_fidx, c->F[0], c->F[1],
+                                              c->F[2], lds, u_dev, red);
+    c->launches++;
+    return (int)grid;
+}
+
+template <typename S>
+void launch_export_t(lbm_ctx *c, double *f_dev) {
+    StateView v = make_view(c);
+    const unsigned grid = nblocks(v.units, 256);
+    if (grid == 0) return;
+    const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    k_export<S><<<grid, 256, 0, c->stream>>>((const S *)cur_pop(c), v, c->d_fidx, lds, f_dev);
+    c->launches++;
+}
+
+template <typename S>
+void launch_import_t(lbm_ctx *c, const double *f_dev) {
+    StateView v = make_view(c);
+    const unsigned grid = nblocks(v.units, 256);
+    if (grid == 0) return;
+    const float sts = c->fp16_scale > 0.f ? c->fp16_scale : 1.0f;
+    // AB: the post-collision state is the current array
+    k_import<S><<<grid, 256, 0, c->stream>>>((S *)cur_pop(c), v, c->d_fidx, sts, f_dev);
+    c->launches++;
+}
+
+template <typename S>
+void launch_export_at_t(lbm_ctx *c, const int64_t *nodes_dev, int count, double *f_dev) {
+    StateView v = make_view(c);
+    const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    k_export_at<S><<<nblocks(count, 256), 256, 0, c->stream>>>((const S *)cur_pop(c), v, c->d_fidx,
+                                                               nodes_dev, count, lds, f_dev);
+    c->launches++;
+}
+
+void launch_export_at(lbm_ctx *c, const int64_t *nodes_dev, int count, double *f_dev) {
+    switch (c->opt.precision) {
+    case LBM_FP64: launch_export_at_t<double>(c, nodes_dev, count, f_dev); break;
+    case LBM_FP32_SHIFTED: launch_export_at_t<float>(c, nodes_dev, count, f_dev); break;
+    default: launch_export_at_t<__half>(c, nodes_dev, count, f_dev); break;
+    }
+}
+
+// Dispatch on the storage precision.
+int launch_step(lbm_ctx *c, bool reduce) {
+    switch (c->opt.precision) {
+    case LBM_FP64: return launch_step_t<double>(c, reduce);
+    case LBM_FP32_SHIFTED: return launch_step_t<float>(c, reduce);
+    default: return launch_step_t<__half>(c, reduce);
+    }
+}
+
+int launch_velocity(lbm_ctx *c, double *u_dev, bool reduce) {
+    switch (c->opt.precision) {
+    case LBM_FP64: return launch_velocity_t<double>(c, u_dev, reduce);
+    case LBM_FP32_SHIFTED: return launch_velocity_t<float>(c, u_dev, reduce);
+    default: return launch_velocity_t<__half>(c, u_dev, reduce);
+    }
+}
+
+void launch_export(lbm_ctx *c, double *f_dev) {
+    switch (c->opt.precision) {
+    case LBM_FP64: launch_export_t<double>(c, f_dev); break;
+    case LBM_FP32_SHIFTED: launch_export_t<float>(c, f_dev); break;
+    default: launch_export_t<__half>(c, f_dev); break;
+    }
+}
+
+void launch_import(lbm_ctx *c, const double *f_dev) {
+    switch (c->opt.precision) {
+    case LBM_FP64: launch_import_t<double>(c, f_dev); break;
+    case LBM_FP32_SHIFTED: launch_import_t<float>(c, f_dev); break;
+    default: launch_import_t<__half>(c, f_dev); break;
+    }
+}
+
+void launch_finalize(lbm_ctx *c, int nblk, double inv_total, double *out_dev) {
+    k_finalize<<<1, 1024, 0, c->stream>>>(c->d_partials, nblk, inv_total, out_dev);
+    c->launches++;
+}
+
+}  // namespace lbm

@@ -1,0 +1,197 @@
+// Link tables built on the device from the voxel mask (setup, once per
+// lattice).
+//
+// Dense layouts keep one 32-bit link word per node: bit 31 = the voxel is
+// solid, bit i (1..18) = the upstream neighbour x - c_i (periodic wrap) is
+// solid, i.e. population i reaches x by halfway bounceback.  The paper's own
+// pre-processing classifies voxels by their 18 neighbours (Sec. 3); this word
+// is that classification per link, so the stream-collide kernel needs a
+// single coalesced 4-byte load instead of 18 mask reads.
+//
+// The sparse layout lists fluid nodes in node order (fluid_idx), gives every
+// fluid node the fluid index of each upstream neighbour (nbr, -1 where solid)
+// and the same bounceback bits (bb).  Per-direction bounceback link counts
+// are accumulated with integer atomics, so they are exact.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ uint32_t upstream(uint32_t n, int j, int Lx, int Ly, int Lz) {
+    uint32_t t = n / (uint32_t)Lx;
+    int x = (int)(n - t * (uint32_t)Lx);
+    int z = (int)(t / (uint32_t)Ly);
+    int y = (int)(t - (uint32_t)z * (uint32_t)Ly);
+    int xs = x - cx(j), ys = y - cy(j), zs = z - cz(j);
+    xs = xs < 0 ? xs + Lx : (xs >= Lx ? xs - Lx : xs);
+    ys = ys < 0 ? ys + Ly : (ys >= Ly ? ys - Ly : ys);
+    zs = zs < 0 ? zs + Lz : (zs >= Lz ? zs - Lz : zs);
+    return (uint32_t)xs + (uint32_t)Lx * ((uint32_t)ys + (uint32_t)Ly * (uint32_t)zs);
+}
+
+// Adds the per-warp popcount of each direction's bounceback flag.
+__device__ __forceinline__ void count_links(uint32_t bits, bool valid,
+                                            unsigned long long *links) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 1; j < Q; ++j) {
+        unsigned b = __ballot_sync(0xffffffffu, valid && (bits & (1u << j)));
+        if (lane == 0 && b) atomicAdd(links + j, (unsigned long long)__popc(b));
+    }
+}
+
+__global__ void k_link_words(const uint8_t *__restrict__ mask, int Lx, int Ly, int Lz,
+                             uint32_t N, uint32_t *__restrict__ lw,
+                             unsigned long long *links) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t bits = 0;
+    bool fluid = false;
+    if (n < N) {
+        if (mask[n]) {
+            bits = SOLID_BIT;
+        } else {
+            fluid = true;
+#pragma unroll
+            for (int j = 1; j < Q; ++j)
+                if (mask[upstream(n, j, Lx, Ly, Lz)]) bits |= 1u << j;
+        }
+        lw[n] = bits;
+    }
+    count_links(bits, fluid, links);
+}
+
+// Fluid count per block of 1024 nodes.
+__global__ void __launch_bounds__(1024) k_count_fluid(const uint8_t *__restrict__ mask, uint32_t N,
+                                                      uint32_t *block_count) {
+    const uint32_t n = blockIdx.x * 1024u + threadIdx.x;
+    const bool f = n < N && mask[n] == 0;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    __shared__ uint32_t sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < 32; ++w) s += sm[w];
+        block_count[blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of the block counts by one block (setup only).
+__global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *count, uint32_t nb,
+                                                      uint32_t *offset, uint32_t *total) {
+    __shared__ uint32_t sm[1024];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? count[i] : 0;
+        sm[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+            uint32_t t = threadIdx.x >= (unsigned)o ? sm[threadIdx.x - o] : 0;
+            __syncthreads();
+            sm[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) offset[i] = carry + sm[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sm[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Writes fluid_idx and the node -> fluid map (-1 for solids).
+__global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ mask, uint32_t N,
+                                                  const uint32_t *__restrict__ offset,
+                                                  int32_t *fidx, int32_t *node2fluid) {
+    const uint32_t n = blockIdx.x * 1024u + threadIdx.x;
+    const bool f = n < N && mask[n] == 0;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    __shared__ uint32_t sm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < 32; ++w) {
+            uint32_t t = sm[w];
+            sm[w] = s;
+            s += t;
+        }
+    }
+    __syncthreads();
+    if (n < N) {
+        if (f) {
+            const uint32_t k = offset[blockIdx.x] + sm[wid] + __popc(b & ((1u << lane) - 1u));
+            fidx[k] = (int32_t)n;
+            node2fluid[n] = (int32_t)k;
+        } else {
+            node2fluid[n] = -1;
+        }
+    }
+}
+
+__global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, int Lx, int Ly,
+                               int Lz, const int32_t *__restrict__ node2fluid, int32_t *nbr,
+                               uint32_t *bb, unsigned long long *links) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t bits = 0;
+    const bool valid = k < Nf;
+    if (valid) {
+        const uint32_t n = (uint32_t)fidx[k];
+#pragma unroll
+        for (int j = 1; j < Q; ++j) {
+            int32_t s = node2fluid[upstream(n, j, Lx, Ly, Lz)];
+            nbr[(size_t)(j - 1) * Nf + k] = s;
+            if (s < 0) bits |= 1u << j;
+        }
+        bb[k] = bits;
+    }
+    count_links(bits, valid, links);
+}
+
+// ---------------------------------------------------------------- launchers
+
+int build_dense_links(lbm_ctx *c, unsigned long long *d_links) {
+    const uint32_t N = (uint32_t)c->N;
+    k_link_words<<<(N + 255) / 256, 256, 0, c->stream>>>(c->d_mask, c->Lx, c->Ly, c->Lz, N,
+                                                          c->d_lw, d_links);
+    c->launches++;
+    return launch_error(cudaGetLastError());
+}
+
+int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
+    const uint32_t N = (uint32_t)c->N;
+    const uint32_t nb = (N + 1023) / 1024;
+    uint32_t *d_cnt = nullptr, *d_off = nullptr, *d_tot = nullptr;
+    int32_t *d_n2f = nullptr;
+    cudaError_t e = cudaMalloc(&d_cnt, sizeof(uint32_t) * (2 * (size_t)nb + 1));
+    if (e != cudaSuccess) return launch_error(e);
+    d_off = d_cnt + nb;
+    d_tot = d_off + nb;
+    e = cudaMalloc(&d_n2f, sizeof(int32_t) * (size_t)N);
+    if (e != cudaSuccess) {
+        cudaFree(d_cnt);
+        return launch_error(e);
+    }
+    k_count_fluid<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_cnt);
+    k_scan_counts<<<1, 1024, 0, c->stream>>>(d_cnt, nb, d_off, d_tot);
+    k_compact<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_off, c->d_fidx, d_n2f);
+    const uint32_t Nf = (uint32_t)c->Nf;
+    if (Nf > 0)
+        k_sparse_links<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_fidx, Nf, c->Lx, c->Ly, c->Lz,
+                                                                 d_n2f, c->d_nbr, c->d_bb, d_links);
+    c->launches += 4;
+    uint32_t tot = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_n2f);
+    cudaFree(d_cnt);
+    if (e != cudaSuccess) return launch_error(e);
+    if ((int64_t)tot != c->Nf) return LBM_ECUDA;
+    return LBM_OK;
+}
+
+}  // namespace lbm

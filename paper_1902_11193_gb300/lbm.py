@@ -1,0 +1,262 @@
+"""ctypes binding of liblbm_gb300.so (the C ABI in include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library cannot be loaded or no
+CUDA device is present the calls raise.
+
+    solver = LBMSolver(mask, set_="B", tau=1.0, force=(1e-6, 0, 0))
+    solver.run_to_convergence(1e-9)
+    k = solver.permeability()          # eq. (perm_calc), lattice units
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+SET_A, SET_B, SET_C, SET_D, SET_E, SET_SRT = range(6)
+SET_NAMES = {"A": SET_A, "B": SET_B, "C": SET_C, "D": SET_D, "E": SET_E, "SRT": SET_SRT}
+FP64, FP32, FP16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
+AB, AA, SPARSE = 0, 1, 2
+LAYOUTS = {"ab": AB, "aa": AA, "sparse": SPARSE}
+
+ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV",
+          -5: "EUNSTABLE", -6: "ETIMEOUT", -7: "ENOSTATE", -8: "EIO"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = f"{what}: {ERRORS.get(code, code)} ({lib().lbm_strerror(code).decode()})"
+        if code == -3:
+            msg += f" [{lib().lbm_last_cuda_error().decode()}]"
+        super().__init__(msg)
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("check_interval", C.c_int32),
+                ("linear_eq", C.c_int32), ("max_steps", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads liblbm_gb300.so, building it in-tree if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LBM_SO
+        if not os.path.exists(path):
+            _build.build_lbm()
+        L = C.CDLL(path)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        sig = {
+            "lbm_default_options": (None, [C.POINTER(Options)]),
+            "lbm_rates": (C.c_int, [i32, dbl, dbl, dp]),
+            "lbm_create": (C.c_int, [C.POINTER(vp), u8p, i32p, i32, dbl, dbl, dp,
+                                     C.POINTER(Options)]),
+            "lbm_create_rates": (C.c_int, [C.POINTER(vp), u8p, i32p, dp, dp, C.POINTER(Options)]),
+            "lbm_destroy": (None, [vp]),
+            "lbm_step": (C.c_int, [vp, i64]),
+            "lbm_run_to_convergence": (C.c_int, [vp, dbl, C.POINTER(i64)]),
+            "lbm_mean_velocity": (C.c_int, [vp, dp]),
+            "lbm_permeability": (C.c_int, [vp, dp]),
+            "lbm_velocity": (C.c_int, [vp, vp]),
+            "lbm_get_populations": (C.c_int, [vp, vp]),
+            "lbm_set_populations": (C.c_int, [vp, vp]),
+            "lbm_get_populations_at": (C.c_int, [vp, vp, i64, vp]),
+            "lbm_link_counts": (C.c_int, [vp, C.POINTER(i64), vp]),
+            "lbm_sparse_tables": (C.c_int, [vp, vp, vp, vp]),
+            "lbm_steps_done": (i64, [vp]),
+            "lbm_kernel_launches": (i64, [vp]),
+            "lbm_save": (C.c_int, [vp, C.c_char_p]),
+            "lbm_load": (C.c_int, [C.POINTER(vp), C.c_char_p, C.POINTER(Options)]),
+            "lbm_strerror": (C.c_char_p, [C.c_int]),
+            "lbm_last_cuda_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise LBMError(rc, what)
+
+
+def rates(set_: int | str, tau: float, Lambda: float = 3.0 / 16.0) -> np.ndarray:
+    """Table 2 relaxation rates s[19] as the library computes them."""
+    s = np.zeros(19)
+    _check(lib().lbm_rates(SET_NAMES[set_] if isinstance(set_, str) else int(set_), float(tau),
+                           float(Lambda), s), "lbm_rates")
+    return s
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().lbm_default_options(C.byref(o))
+    return o
+
+
+class LBMSolver:
+    """One lattice on the current CUDA device (one context = one C-ABI handle).
+
+    mask: uint8 [Lz, Ly, Lx], 1 = solid.  Either (set_, tau, Lambda) or
+    explicit rates s[19].  stream: a cudaStream_t handle (int) or a
+    torch.cuda.Stream; None lets the library create its own stream.
+    """
+
+    def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
+                 rates_=None, precision="fp32", layout="aa", check_interval=100,
+                 linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
+                 block_size=0):
+        self.mask = np.ascontiguousarray(mask, np.uint8)
+        if self.mask.ndim != 3:
+            raise ValueError("mask must be [Lz, Ly, Lx]")
+        self.dims = np.array(self.mask.shape[::-1], np.int32)
+        self.N = int(self.mask.size)
+        self.force = np.ascontiguousarray(force, np.float64)
+        o = default_options()
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        o.check_interval = int(check_interval)
+        o.linear_eq = int(bool(linear_eq))
+        o.max_steps = int(max_steps)
+        o.fp16_scale_log2 = int(fp16_scale_log2)
+        o.block_size = int(block_size)
+        if stream is not None:
+            o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        self.options = o
+        h = C.c_void_p()
+        if rates_ is not None:
+            s = np.ascontiguousarray(rates_, np.float64)
+            rc = lib().lbm_create_rates(C.byref(h), self.mask, self.dims, s, self.force, C.byref(o))
+            self.tau = 1.0 / s[9]
+        else:
+            st = SET_NAMES[set_] if isinstance(set_, str) else int(set_)
+            rc = lib().lbm_create(C.byref(h), self.mask, self.dims, st, float(tau), float(Lambda),
+                                  self.force, C.byref(o))
+            self.tau = float(tau)
+        _check(rc, "lbm_create")
+        self._h = h
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "LBMSolver":
+        h = C.c_void_p()
+        o = default_options()
+        if stream is not None:
+            o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        _check(lib().lbm_load(C.byref(h), path.encode(), C.byref(o)), "lbm_load")
+        self = cls.__new__(cls)
+        self._h = h
+        with open(path, "rb") as fh:  # header: magic, version, dims, s[19], F[3]
+            head = fh.read(8 + 4 + 12 + 152 + 24)
+        dims = np.frombuffer(head[12:24], np.int32)
+        s = np.frombuffer(head[24:176], np.float64)
+        self.dims = dims.copy()
+        self.N = int(np.prod(dims))
+        self.force = np.frombuffer(head[176:200], np.float64).copy()
+        self.tau = 1.0 / s[9]
+        self.mask = None
+        return self
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------- stepping
+    def step(self, n: int = 1) -> None:
+        _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def run_to_convergence(self, tol: float, raise_on_failure: bool = True):
+        """Returns (status code, steps taken by this call)."""
+        steps = C.c_int64(0)
+        rc = lib().lbm_run_to_convergence(self._h, float(tol), C.byref(steps))
+        if rc not in (0, -4) and raise_on_failure:
+            raise LBMError(rc, "lbm_run_to_convergence")
+        return rc, int(steps.value)
+
+    # -------------------------------------------------------------- outputs
+    def mean_velocity(self) -> np.ndarray:
+        U = np.zeros(3)
+        _check(lib().lbm_mean_velocity(self._h, U), "lbm_mean_velocity")
+        return U
+
+    def permeability(self) -> np.ndarray:
+        k = np.zeros(3)
+        _check(lib().lbm_permeability(self._h, k), "lbm_permeability")
+        return k
+
+    def velocity(self) -> np.ndarray:
+        u = np.zeros(3 * self.N)
+        _check(lib().lbm_velocity(self._h, u.ctypes.data), "lbm_velocity")
+        return u.reshape((3,) + tuple(self.dims[::-1]))
+
+    def get_populations(self) -> np.ndarray:
+        f = np.zeros(19 * self.N)
+        _check(lib().lbm_get_populations(self._h, f.ctypes.data), "lbm_get_populations")
+        return f.reshape((19,) + tuple(self.dims[::-1]))
+
+    def set_populations(self, f: np.ndarray) -> None:
+        f = np.ascontiguousarray(f, np.float64).reshape(-1)
+        if f.size != 19 * self.N:
+            raise ValueError("populations must have 19*N entries")
+        _check(lib().lbm_set_populations(self._h, f.ctypes.data), "lbm_set_populations")
+
+    def get_populations_at(self, nodes) -> np.ndarray:
+        """Post-collision populations f[len(nodes), 19] at node indices."""
+        nodes = np.ascontiguousarray(nodes, np.int64).reshape(-1)
+        f = np.zeros((len(nodes), 19))
+        _check(lib().lbm_get_populations_at(self._h, nodes.ctypes.data, len(nodes), f.ctypes.data),
+               "lbm_get_populations_at")
+        return f
+
+    def link_counts(self):
+        nf = C.c_int64(0)
+        links = np.zeros(19, np.int64)
+        _check(lib().lbm_link_counts(self._h, C.byref(nf), links.ctypes.data), "lbm_link_counts")
+        return int(nf.value), links
+
+    def sparse_tables(self):
+        nf, _ = self.link_counts()
+        fi = np.zeros(max(nf, 1), np.int32)
+        nbr = np.zeros(max(18 * nf, 1), np.int32)
+        bb = np.zeros(max(nf, 1), np.uint32)
+        _check(lib().lbm_sparse_tables(self._h, fi.ctypes.data, nbr.ctypes.data, bb.ctypes.data),
+               "lbm_sparse_tables")
+        return fi[:nf], nbr[: 18 * nf].reshape(18, nf), bb[:nf]
+
+    @property
+    def steps(self) -> int:
+        return int(lib().lbm_steps_done(self._h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().lbm_kernel_launches(self._h))
+
+    def save(self, path: str) -> None:
+        _check(lib().lbm_save(self._h, path.encode()), "lbm_save")

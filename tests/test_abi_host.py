@@ -1,0 +1,70 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads
+and exports every entry point include/lbm.h declares; its Table 2 rates agree
+with the oracle's; argument validation rejects bad inputs before any device
+work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1902_11193_gb300 import _build, lbm
+
+    _build.build_lbm()
+    return lbm
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared("lbm.h")
+    assert "lbm_create" in names and "lbm_run_to_convergence" in names
+    so = C.CDLL(L._build.LBM_SO)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("st", ["A", "B", "C", "D", "E", "SRT"])
+@pytest.mark.parametrize("tau", [0.55, 0.8, 1.0, 1.6, 2.0])
+def test_rates_match_oracle(L, ora, st, tau):
+    for lam in (1 / 64, 3 / 16, 3 / 8, 1.0):
+        assert np.array_equal(L.rates(st, tau, lam), ora.rates(st, tau, lam))
+
+
+def test_create_rejects_bad_arguments(L):
+    m = np.zeros((4, 4, 4), np.uint8)
+    with pytest.raises(L.LBMError) as e:
+        L.LBMSolver(m, "B", tau=0.5)
+    assert e.value.code == -1
+    with pytest.raises(L.LBMError):
+        L.LBMSolver(m, "E", tau=1.0, Lambda=0.0)
+    bad = m.copy()
+    bad[0, 0, 0] = 2
+    with pytest.raises(L.LBMError):
+        L.LBMSolver(bad, "B", tau=1.0)
+    with pytest.raises(L.LBMError):
+        L.LBMSolver(m, "B", tau=1.0, block_size=48)
+    s = L.rates("B", 1.0)
+    s[4] = 2.5
+    with pytest.raises(L.LBMError):
+        L.LBMSolver(m, rates_=s)
+    s = L.rates("B", 1.0)
+    s[6] = 0.9  # one rate per moment group
+    with pytest.raises(L.LBMError):
+        L.LBMSolver(m, rates_=s)
+
+
+def test_strerror_covers_codes(L):
+    lib = L.lib()
+    for code in range(0, -9, -1):
+        assert lib.lbm_strerror(code).decode() != "unknown error"
