@@ -84,6 +84,14 @@ def lib():
         L.ora_run_to_convergence.restype = C.c_int
         L.ora_set_threads.argtypes = [C.c_int]
         L.ora_get_threads.restype = C.c_int
+        L.ora_rates_magic.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.ora_rates_magic.restype = C.c_int
+        L.ora_stream_field.argtypes = [C.c_void_p, dp, dp]
+        L.ora_unstream_field.argtypes = [C.c_void_p, dp, dp]
+        L.ora_adjoint_apply.argtypes = [C.c_void_p, dp, dp]
+        L.ora_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double,
+                                  C.c_int64, C.c_int64, dp, C.POINTER(C.c_int64)]
+        L.ora_adjoint.restype = C.c_int
         _lib = L
     return _lib
 
@@ -118,6 +126,17 @@ def rates(set_: int | str, tau: float, Lambda: float = 3.0 / 16.0) -> np.ndarray
     if lib().ora_rates(int(set_), float(tau), float(Lambda), s) != 0:
         raise ValueError(f"invalid rate parameters set={set_} tau={tau} Lambda={Lambda}")
     return s
+
+
+def rates_magic(tau: float, Lq: float, Lm: float) -> np.ndarray:
+    """Sets B/D/E with the odd rates given by their magic parameters."""
+    s = np.zeros(19)
+    if lib().ora_rates_magic(float(tau), float(Lq), float(Lm), s) != 0:
+        raise ValueError("invalid magic parameters")
+    return s
+
+
+GRAD_KEYS = ("dtau", "dLambda", "dLambda_q", "dLambda_m", "dFx", "dFy", "dFz")
 
 
 def meq(rho: float, j, linear: bool = False) -> np.ndarray:
@@ -219,6 +238,32 @@ class Solver:
         rc = lib().ora_run_to_convergence(self._h, float(tol), int(K), int(max_steps),
                                           C.byref(steps), U)
         return rc, int(steps.value), U
+
+    def stream_field(self, f: np.ndarray) -> np.ndarray:
+        out = np.zeros(19 * self.N)
+        lib().ora_stream_field(self._h, np.ascontiguousarray(f, np.float64).reshape(-1), out)
+        return out.reshape((19,) + self.mask.shape)
+
+    def unstream_field(self, f: np.ndarray) -> np.ndarray:
+        out = np.zeros(19 * self.N)
+        lib().ora_unstream_field(self._h, np.ascontiguousarray(f, np.float64).reshape(-1), out)
+        return out.reshape((19,) + self.mask.shape)
+
+    def adjoint_apply(self, psi: np.ndarray) -> np.ndarray:
+        """J_C(h)^T S^T psi at the current state (h = S f*)."""
+        out = np.zeros(19 * self.N)
+        lib().ora_adjoint_apply(self._h, np.ascontiguousarray(psi, np.float64).reshape(-1), out)
+        return out.reshape((19,) + self.mask.shape)
+
+    def adjoint(self, set_, tau: float, Lambda: float = 3.0 / 16.0, tol: float = 1e-12,
+                K: int = 10, max_iter: int = 10**6):
+        """Steady fixed-point adjoint: returns (rc, gradient dict, iterations)."""
+        st = SET_NAMES[set_] if isinstance(set_, str) else int(set_)
+        g = np.zeros(7)
+        it = C.c_int64(0)
+        rc = lib().ora_adjoint(self._h, st, float(tau), float(Lambda), float(tol), int(K),
+                               int(max_iter), g, C.byref(it))
+        return rc, dict(zip(GRAD_KEYS, g)), int(it.value)
 
     def permeability(self, tau: float) -> np.ndarray:
         """eq. (perm_calc) with body forcing: k_j = nu <u_j> / F_j, nu = (tau - 1/2)/3."""

@@ -445,3 +445,247 @@ int ora_get_threads(void) {
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------- adjoint
+ *
+ * Not part of the paper: the sensitivity of the steady permeability to the
+ * parameters (tau, the magic parameters, the force), written from the
+ * definition of a fixed-point adjoint.  In the streamed variable h = S f*
+ * one time step is h -> S C(h); at the steady state the adjoint psi solves
+ * psi = J_C(h)^T S^T psi + dJ/dh with J = k along the drive, and
+ * dk/dtheta = dJ/dtheta + (S^T psi) . dC/dtheta.  The collision C is a
+ * quadratic polynomial in h and in F (and linear in each rate), so central
+ * differences give its Jacobian and its F-derivative exactly up to rounding;
+ * tau and Lambda enter through rational rate formulas and are differenced
+ * with a small step. */
+
+int ora_rates_magic(double tau, double Lq, double Lm, double s[Q]) {
+    if (!(tau > 0.5) || !(Lq > 0.0) || !(Lm > 0.0)) return -1;
+    double sn = 1.0 / tau;
+    double sq = 2.0 * (2.0 - sn) / (4.0 * Lq * sn - sn + 2.0);
+    double sm = 2.0 * (2.0 - sn) / (4.0 * Lm * sn - sn + 2.0);
+    double t[Q] = {0.0, sn, sn, 0.0, sq, 0.0, sq, 0.0, sq, sn,
+                   sn, sn, sn, sn, sn, sn, sm, sm, sm};
+    for (int k = 0; k < Q; ++k) s[k] = t[k];
+    return 0;
+}
+
+void ora_stream_field(ora_solver *h, const double *in, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < h->Lz; ++z) {
+        double fl[Q];
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) {
+                    for (int i = 0; i < Q; ++i) out[i * h->N + n] = in[i * h->N + n];
+                    continue;
+                }
+                pull(h, in, x, y, z, fl);
+                for (int i = 0; i < Q; ++i) out[i * h->N + n] = fl[i];
+            }
+    }
+}
+
+/* (S^T v)(x, j): the post-collision population j of x streams to x + c_j
+ * when that voxel is fluid, else it is bounced into slot opp(j) of x. */
+static void unstream_node(const ora_solver *h, const double *v, int x, int y, int z,
+                          double out[Q]) {
+    int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+    for (int j = 0; j < Q; ++j) {
+        int xd = wrapi(x + CV[j][0], h->Lx), yd = wrapi(y + CV[j][1], h->Ly),
+            zd = wrapi(z + CV[j][2], h->Lz);
+        int64_t nd = xd + (int64_t)h->Lx * (yd + (int64_t)h->Ly * zd);
+        out[j] = h->solid[nd] ? v[OPP[j] * h->N + n] : v[j * h->N + nd];
+    }
+}
+
+void ora_unstream_field(ora_solver *h, const double *in, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < h->Lz; ++z) {
+        double o[Q];
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) {
+                    for (int i = 0; i < Q; ++i) out[i * h->N + n] = in[i * h->N + n];
+                    continue;
+                }
+                unstream_node(h, in, x, y, z, o);
+                for (int i = 0; i < Q; ++i) out[i * h->N + n] = o[i];
+            }
+    }
+}
+
+/* Collision Jacobian J[i][c] = dC_i/dh_c at h: exact central differences
+ * (C is quadratic in h). */
+static void collide_jacobian(const double hs[Q], const double s[Q], const double F[3],
+                             int linear, double J[Q][Q]) {
+    const double d = 0.125;
+    double hp[Q], hm[Q], cp[Q], cm[Q];
+    for (int c = 0; c < Q; ++c) {
+        for (int i = 0; i < Q; ++i) hp[i] = hm[i] = hs[i];
+        hp[c] += d;
+        hm[c] -= d;
+        ora_collide(hp, s, F, linear, cp);
+        ora_collide(hm, s, F, linear, cm);
+        for (int i = 0; i < Q; ++i) J[i][c] = (cp[i] - cm[i]) / (2.0 * d);
+    }
+}
+
+void ora_adjoint_apply(ora_solver *h, const double *in, double *out) {
+    double *hs = (double *)malloc(sizeof(double) * Q * (size_t)h->N);
+    ora_stream_field(h, h->f, hs);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < h->Lz; ++z) {
+        double hn[Q], phi[Q], J[Q][Q];
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) {
+                    for (int i = 0; i < Q; ++i) out[i * h->N + n] = 0.0;
+                    continue;
+                }
+                for (int i = 0; i < Q; ++i) hn[i] = hs[i * h->N + n];
+                collide_jacobian(hn, h->s, h->F, h->linear, J);
+                unstream_node(h, in, x, y, z, phi);
+                for (int c = 0; c < Q; ++c) {
+                    double acc = 0.0;
+                    for (int i = 0; i < Q; ++i) acc += J[i][c] * phi[i];
+                    out[c * h->N + n] = acc;
+                }
+            }
+    }
+    free(hs);
+}
+
+/* Rates for a parameter point of the given set: p = {tau, Lambda, Lq, Lm};
+ * the magic-parameter sets (B, D, E) are evaluated through Lq and Lm so that
+ * they can be differentiated in each. */
+static int rates_at(int set, const double p[4], double s[Q]) {
+    if (set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E)
+        return ora_rates_magic(p[0], p[2], p[3], s);
+    return ora_rates(set, p[0], p[1], s);
+}
+
+int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, int64_t K,
+                int64_t max_iter, double grad[7], int64_t *iters) {
+    init_tables();
+    int d = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(h->F[a]) > fabs(h->F[d])) d = a;
+    if (h->F[d] == 0.0) return -1;
+    double p0[4] = {tau, Lambda, 3.0 / 16.0, 3.0 / 16.0};
+    if (set == ORA_SET_D) p0[3] = 3.0 / 8.0;
+    if (set == ORA_SET_E) p0[2] = p0[3] = Lambda;
+    double s0[Q];
+    if (rates_at(set, p0, s0) != 0) return -1;
+    for (int k = 0; k < Q; ++k)
+        if (fabs(s0[k] - h->s[k]) > 1e-14) return -1; /* rates must match the solver */
+    if (K < 1) K = 1;
+
+    const int64_t N = h->N;
+    double *hs = (double *)malloc(sizeof(double) * Q * (size_t)N);
+    ora_stream_field(h, h->f, hs);
+    int64_t Nf = 0;
+    for (int64_t n = 0; n < N; ++n) Nf += !h->solid[n];
+    const double nu = (tau - 0.5) / 3.0;
+    /* dJ/dh_i(x) = nu c_{i,d} / (F_d N) at fluid nodes, J = nu U_d / F_d */
+    double *g = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *psi = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *nxt = (double *)calloc((size_t)Q * N, sizeof(double));
+    double Ud = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        if (h->solid[n]) continue;
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            g[i * N + n] = nu * CV[i][d] / (h->F[d] * (double)N);
+            acc += CV[i][d] * hs[i * N + n];
+        }
+        Ud += acc + 0.5 * h->F[d];
+    }
+    Ud /= (double)N;
+    memcpy(psi, g, sizeof(double) * Q * (size_t)N);
+    int rc = 1;
+    int64_t it = 0;
+    while (it < max_iter) {
+        ora_adjoint_apply(h, psi, nxt);
+        double dmax = 0.0, pmax = 0.0;
+        for (int64_t q = 0; q < (int64_t)Q * N; ++q) {
+            nxt[q] += g[q];
+            double dd = fabs(nxt[q] - psi[q]);
+            if (dd > dmax) dmax = dd;
+            if (fabs(nxt[q]) > pmax) pmax = fabs(nxt[q]);
+        }
+        double *t = psi;
+        psi = nxt;
+        nxt = t;
+        ++it;
+        if (it % K == 0 && dmax <= tol * pmax) {
+            rc = 0;
+            break;
+        }
+    }
+    /* phi = S^T psi; gradient contributions per parameter */
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int z = 0; z < h->Lz; ++z)
+        for (int y = 0; y < h->Ly; ++y)
+            for (int x = 0; x < h->Lx; ++x) {
+                int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->solid[n]) continue;
+                double hn[Q], phi[Q], cp[Q], cm[Q], sp[Q], sm[Q];
+                for (int i = 0; i < Q; ++i) hn[i] = hs[i * N + n];
+                unstream_node(h, psi, x, y, z, phi);
+                /* parameters 0..3: tau, Lambda, Lq, Lm */
+                const double dp[4] = {1e-5, 1e-5, 1e-5, 1e-5};
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 1 && set != ORA_SET_E) continue;
+                    if ((q == 2 || q == 3) &&
+                        !(set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E))
+                        continue;
+                    double pp[4], pm[4];
+                    for (int r = 0; r < 4; ++r) pp[r] = pm[r] = p0[r];
+                    if (q == 1) { /* Set E: Lambda moves both magic parameters */
+                        pp[2] += dp[1]; pp[3] += dp[1];
+                        pm[2] -= dp[1]; pm[3] -= dp[1];
+                    } else {
+                        pp[q] += dp[q];
+                        pm[q] -= dp[q];
+                    }
+                    rates_at(set, pp, sp);
+                    rates_at(set, pm, sm);
+                    ora_collide(hn, sp, h->F, h->linear, cp);
+                    ora_collide(hn, sm, h->F, h->linear, cm);
+                    double sum = 0.0;
+                    for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dp[q]);
+                    acc[q] += sum;
+                }
+                /* force components: C is quadratic in F */
+                const double dF = 0.5 * fabs(h->F[d]);
+                for (int a = 0; a < 3; ++a) {
+                    double Fp[3] = {h->F[0], h->F[1], h->F[2]}, Fm[3] = {h->F[0], h->F[1], h->F[2]};
+                    Fp[a] += dF;
+                    Fm[a] -= dF;
+                    ora_collide(hn, h->s, Fp, h->linear, cp);
+                    ora_collide(hn, h->s, Fm, h->linear, cm);
+                    double sum = 0.0;
+                    for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dF);
+                    acc[4 + a] += sum;
+                }
+            }
+    /* explicit dependence of J = nu(tau) U_d(h, F) / F_d on the parameters */
+    grad[0] = acc[0] + Ud / (3.0 * h->F[d]);
+    const int magic = set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E;
+    grad[1] = set == ORA_SET_E ? acc[1] : (magic ? acc[2] + acc[3] : NAN);
+    grad[2] = magic ? acc[2] : NAN;
+    grad[3] = magic ? acc[3] : NAN;
+    for (int a = 0; a < 3; ++a) grad[4 + a] = acc[4 + a];
+    grad[4 + d] += nu * ((double)Nf / (2.0 * (double)N)) / h->F[d] -
+                   nu * Ud / (h->F[d] * h->F[d]);
+    if (iters) *iters = it;
+    free(hs);
+    free(g);
+    free(psi);
+    free(nxt);
+    return rc;
+}

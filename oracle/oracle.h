@@ -73,6 +73,32 @@ int ora_run_to_convergence(ora_solver *h, double tol, int64_t K, int64_t max_ste
 void ora_set_threads(int n);
 int ora_get_threads(void);
 
+/* Rates of the TRT-like sets (B, D, E) with the odd rates given by their
+ * magic parameters: s_q from Lambda_q, s_m from Lambda_m (eq. Magic param),
+ * even rates s_nu = 1/tau.  Set B is (3/16, 3/16), Set D (3/16, 3/8), Set E
+ * (Lambda, Lambda). */
+int ora_rates_magic(double tau, double Lq, double Lm, double s[19]);
+
+/* Streaming as a linear map on whole fields [19][N]: out = S in (pull with
+ * halfway bounceback) and out = S^T in (its transpose, S^-1).  Solid nodes
+ * are copied through. */
+void ora_stream_field(ora_solver *h, const double *in, double *out);
+void ora_unstream_field(ora_solver *h, const double *in, double *out);
+/* One adjoint step without source: out = J_C(h)^T S^T in, where h = S f* is
+ * the streamed current state and J_C the per-node collision Jacobian. */
+void ora_adjoint_apply(ora_solver *h, const double *in, double *out);
+
+/* Steady fixed-point adjoint of k along the drive (largest |F_j|):
+ * psi = J_C^T S^T psi + dk/dh, iterated from psi = dk/dh until the largest
+ * change is <= tol times the largest |psi| (checked every K iterations).
+ * The gradient is dk/dtheta = dJ/dtheta + (S^T psi) . dC/dtheta.
+ * (set, tau, Lambda) must be the parameters the solver's rates came from.
+ * grad = {dk/dtau, dk/dLambda, dk/dLambda_q, dk/dLambda_m, dk/dF_x,
+ * dk/dF_y, dk/dF_z}; the Lambda entries are NaN for sets without magic
+ * parameters (A, C, SRT).  Returns 0, 1 (not converged) or -1. */
+int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, int64_t K,
+                int64_t max_iter, double grad[7], int64_t *iters);
+
 #ifdef __cplusplus
 }
 #endif
