@@ -264,7 +264,10 @@ def run_ours(args):
 
     dist, rank, ws, local = dist_setup(args)
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the default stream's handle is 0, which the library
+    # would replace by a stream of its own), current for torch's events too
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     mask, nspheres = workload(args.size)
     nf = int((mask == 0).sum())
     N = mask.size

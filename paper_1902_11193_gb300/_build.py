@@ -20,7 +20,7 @@ GEOM_SO = os.path.join(LIBDIR, "libgeom.so")
 LBM_SO = os.path.join(LIBDIR, "liblbm_gb300.so")
 
 CUDA_SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_links.cu"]
-CUDA_HEADERS = ["lbm_internal.cuh", "lbm_collide.cuh"]
+CUDA_HEADERS = ["lbm_internal.cuh", "lbm_collide.cuh", "lbm_sparse.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

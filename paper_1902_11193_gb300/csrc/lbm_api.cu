@@ -20,6 +20,7 @@ void launch_export_at(lbm_ctx *c, const int64_t *nodes_dev, int count, double *f
 void launch_finalize(lbm_ctx *c, int nblk, double inv_total, double *out_dev);
 int build_dense_links(lbm_ctx *c, unsigned long long *d_links);
 int build_sparse_links(lbm_ctx *c, unsigned long long *d_links);
+int export_sparse_nbr(lbm_ctx *c, int32_t *nbr_dev);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -93,8 +94,9 @@ static void free_ctx(lbm_ctx *c) {
     cudaFree(c->d_mask);
     cudaFree(c->d_lw);
     cudaFree(c->d_fidx);
-    cudaFree(c->d_nbr);
     cudaFree(c->d_bb);
+    cudaFree(c->d_rw);
+    cudaFree(c->d_rstart);
     cudaFree(c->d_pop[0]);
     cudaFree(c->d_pop[1]);
     cudaFree(c->d_partials);
@@ -194,8 +196,11 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     const bool sparse = o.layout == LBM_LAYOUT_SPARSE;
     if (sparse) {
         CKF(cudaMalloc(&c->d_fidx, sizeof(int32_t) * (size_t)(Nf > 0 ? Nf : 1)));
-        CKF(cudaMalloc(&c->d_nbr, sizeof(int32_t) * 18 * (size_t)(Nf > 0 ? Nf : 1)));
         CKF(cudaMalloc(&c->d_bb, sizeof(uint32_t) * (size_t)(Nf > 0 ? Nf : 1)));
+        c->Wr = (c->Lx + 31) / 32;
+        const size_t nrows = (size_t)c->Ly * c->Lz;
+        CKF(cudaMalloc(&c->d_rw, sizeof(RowWord) * nrows * c->Wr));
+        CKF(cudaMalloc(&c->d_rstart, sizeof(int32_t) * (nrows + 1)));
         rc = build_sparse_links(c, d_links);
     } else {
         CKF(cudaMalloc(&c->d_lw, sizeof(uint32_t) * (size_t)N));
@@ -432,7 +437,18 @@ int lbm_sparse_tables(lbm_ctx *c, int32_t *fidx, int32_t *nbr, uint32_t *bb) {
     const size_t Nf = (size_t)c->Nf;
     if (Nf == 0) return LBM_OK;
     if (fidx) CK(cudaMemcpyAsync(fidx, c->d_fidx, 4 * Nf, cudaMemcpyDeviceToHost, c->stream));
-    if (nbr) CK(cudaMemcpyAsync(nbr, c->d_nbr, 4 * 18 * Nf, cudaMemcpyDeviceToHost, c->stream));
+    if (nbr) {
+        int32_t *d_nbr = nullptr;
+        CK(cudaMalloc(&d_nbr, 4 * 18 * Nf));
+        int rc = export_sparse_nbr(c, d_nbr);
+        cudaError_t e = cudaSuccess;
+        if (rc == LBM_OK)
+            e = cudaMemcpyAsync(nbr, d_nbr, 4 * 18 * Nf, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(d_nbr);
+        if (rc != LBM_OK) return rc;
+        if (e != cudaSuccess) return launch_error(e);
+    }
     if (bb) CK(cudaMemcpyAsync(bb, c->d_bb, 4 * Nf, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;

@@ -80,6 +80,40 @@ struct Store<__half> {
     }
 };
 
+// Sparse-layout row metadata, one entry per 32-voxel word of an x-row
+// (row R = y + Ly*z): bit b of `bits` is set iff voxel x = 32w + b is fluid;
+// `base` is the fluid index of the first fluid node at x >= 32w of the row
+// (equivalently the number of fluid nodes before that position in node
+// order).  The fluid index of a fluid voxel (x, R) is then
+// base + popc(bits & ((1 << (x & 31)) - 1)).
+struct __align__(8) RowWord {
+    uint32_t bits;
+    int32_t base;
+};
+
+// Everything the sparse kernels need to find upstream fluid indices.
+// mLx, mLy: ceil(2^64 / L), so that floor(n / L) = umul64hi(n, m) for any
+// n < 2^32 and L < 2^31 (the rounding error n (m - 2^64/L) / 2^64 stays below
+// 2^-32, smaller than the distance 1/L of a non-integer n/L to the next
+// integer).
+struct SparseMap {
+    const int32_t *fidx;
+    const uint32_t *bb;
+    const RowWord *rw;
+    const int32_t *rstart;
+    int Lx, Ly, Lz, Wr;
+    uint64_t mLx, mLy;
+};
+
+__host__ __forceinline__ uint64_t div_magic(uint32_t L) {
+    // ceil(2^64 / L) for L >= 2; L == 1 is handled by the caller
+    return L <= 1 ? 0 : (~uint64_t(0)) / L + 1;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t L, uint64_t m) {
+    return L == 1 ? n : (uint32_t)__umul64hi((uint64_t)n, m);
+}
+
 // Per-launch reduction target: per-block partial sums of (ux, uy, uz) in
 // double, and a device flag raised on non-finite density or momentum.
 struct Reduce {
@@ -105,8 +139,10 @@ struct lbm_ctx {
     uint8_t *d_mask;      // [N]
     uint32_t *d_lw;       // [N] dense link words (AB, AA)
     int32_t *d_fidx;      // [Nf] sparse: node index of each fluid node
-    int32_t *d_nbr;       // [18][Nf] sparse: fluid index of x - c_i, -1 if solid
     uint32_t *d_bb;       // [Nf] sparse: bounceback bits
+    lbm::RowWord *d_rw;   // [Ly*Lz][Wr] sparse: row fluid bits + fluid index base
+    int32_t *d_rstart;    // [Ly*Lz + 1] sparse: fluid index of each row's first node
+    int Wr;               // 32-voxel words per row
     void *d_pop[2];       // populations; AB uses both, AA and SPARSE one
     size_t elem;          // bytes per stored population value
     float fp16_scale;     // 2^S (FP16 storage)

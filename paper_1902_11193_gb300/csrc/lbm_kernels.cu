@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include "lbm_collide.cuh"
+#include "lbm_sparse.cuh"
 
 namespace lbm {
 
@@ -146,28 +147,34 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
-template <typename S, bool ODD>
-__global__ void __launch_bounds__(256) k_sparse(S *A, const int32_t *__restrict__ nbr,
-                                                const uint32_t *__restrict__ bb, uint32_t Nf,
-                                                Collide<typename Store<S>::C> p, float ld_scale,
-                                                float st_scale, Reduce red) {
+// Minimum resident blocks per SM for the sparse stream-collide (caps the
+// registers per thread; more resident warps hide the odd step's dependent
+// index loads).
+#ifndef LBM_SPARSE_MIN_BLOCKS
+#define LBM_SPARSE_MIN_BLOCKS 4
+#endif
+
+// Idx: type of the flat population offsets; uint32_t whenever 19 * Nf < 2^32.
+template <typename S, bool ODD, typename Idx>
+__global__ void __launch_bounds__(256, LBM_SPARSE_MIN_BLOCKS)
+    k_sparse(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p, float ld_scale,
+             float st_scale, Reduce red) {
     using C = typename Store<S>::C;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool fluid = k < Nf;
     C jx = C(0), jy = C(0), jz = C(0);
     if (fluid) {
-        size_t loc[Q];
+        Idx loc[Q];
         if (ODD) {
-            const uint32_t bits = bb[k];
+            SparseNode sn;
+            sn.init(k, m);
             loc[0] = k;
 #pragma unroll
             for (int j = 1; j < Q; ++j)
-                loc[j] = (bits & (1u << j))
-                             ? (size_t)j * Nf + k
-                             : (size_t)opp(j) * Nf + (uint32_t)nbr[(size_t)(j - 1) * Nf + k];
+                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up(j, m);
         } else {
 #pragma unroll
-            for (int j = 0; j < Q; ++j) loc[j] = (size_t)j * Nf + k;
+            for (int j = 0; j < Q; ++j) loc[j] = (Idx)j * Nf + k;
         }
         C g[Q];
 #pragma unroll
@@ -212,16 +219,21 @@ struct StateView {
     int parity;      // steps % 2 (AA, SPARSE)
     uint32_t units;  // N (dense) or Nf (sparse)
     const uint32_t *lw;
-    const int32_t *nbr;
-    const uint32_t *bb;
+    SparseMap sm;
     Dims d;
+};
+
+struct UnitNode {
+    DenseNode d;
+    SparseNode s;
 };
 
 // Returns the flat offset for unit u, direction j.  For AB, kind 0 reads the
 // pull location in the current array and kind 1 the node's own slot
 // (holding f*_opp(j) for slot opp(j)).
 __device__ __forceinline__ size_t state_loc(const StateView &v, uint32_t u, int j, int kind,
-                                            uint32_t w, const DenseNode &nd) {
+                                            uint32_t w, const UnitNode &un) {
+    const DenseNode &nd = un.d;
     if (v.layout == LBM_LAYOUT_AB) {
         if (kind == 1) return (size_t)opp(j) * v.units + u;  // f*_opp(j) lives in slot opp(j)
         if (j == 0) return u;
@@ -233,20 +245,20 @@ __device__ __forceinline__ size_t state_loc(const StateView &v, uint32_t u, int 
     const bool odd = (kind == 0) ? (v.parity == 1) : (v.parity == 0);
     if (!odd || j == 0 || (w & (1u << j))) return (size_t)j * v.units + u;
     if (v.layout == LBM_LAYOUT_AA) return (size_t)opp(j) * v.units + nd.up(j);
-    return (size_t)opp(j) * v.units + (uint32_t)v.nbr[(size_t)(j - 1) * v.units + u];
+    return (size_t)opp(j) * v.units + un.s.up(j, v.sm);
 }
 
 __device__ __forceinline__ bool state_unit(const StateView &v, uint32_t u, uint32_t &node,
-                                           uint32_t &w, DenseNode &nd) {
+                                           uint32_t &w, UnitNode &un) {
+    node = u;
     if (v.layout == LBM_LAYOUT_SPARSE) {
-        w = v.bb[u];
-        node = u;
+        un.s.init(u, v.sm);
+        w = un.s.bits;
         return true;
     }
     w = v.lw[u];
-    node = u;
     if (w & SOLID_BIT) return false;
-    nd.init(u, v.d);
+    un.d.init(u, v.d);
     return true;
 }
 
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(256) k_velocity(const S *A, StateView v,
     double jx = 0.0, jy = 0.0, jz = 0.0;
     if (u < v.units) {
         uint32_t node, w;
-        DenseNode nd;
+        UnitNode nd;
         fluid = state_unit(v, u, node, w, nd);
         if (fluid) {
 #pragma unroll
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(256) k_export(const S *A, StateView v,
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= v.units) return;
     uint32_t node, w;
-    DenseNode nd;
+    UnitNode nd;
     if (!state_unit(v, u, node, w, nd)) return;
     const size_t out = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
 #pragma unroll
@@ -314,7 +326,7 @@ __global__ void __launch_bounds__(256) k_import(S *A, StateView v, const int32_t
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= v.units) return;
     uint32_t node, w;
-    DenseNode nd;
+    UnitNode nd;
     if (!state_unit(v, u, node, w, nd)) return;
     const size_t in = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
 #pragma unroll
@@ -337,26 +349,29 @@ __global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
     uint32_t unit = node;
     bool fluid;
     uint32_t w = 0;
-    DenseNode nd;
+    UnitNode nd;
     if (v.layout == LBM_LAYOUT_SPARSE) {
         int lo = 0, hi = (int)v.units - 1;
         fluid = false;
         while (lo <= hi) {
             const int mid = (lo + hi) >> 1;
-            const uint32_t m = (uint32_t)fidx[mid];
-            if (m == node) {
+            const uint32_t mv = (uint32_t)fidx[mid];
+            if (mv == node) {
                 fluid = true;
                 unit = (uint32_t)mid;
                 break;
             }
-            if (m < node) lo = mid + 1;
+            if (mv < node) lo = mid + 1;
             else hi = mid - 1;
         }
-        if (fluid) w = v.bb[unit];
+        if (fluid) {
+            nd.s.init(unit, v.sm);
+            w = nd.s.bits;
+        }
     } else {
         w = v.lw[node];
         fluid = !(w & SOLID_BIT);
-        if (fluid) nd.init(node, v.d);
+        if (fluid) nd.d.init(node, v.d);
     }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -369,6 +384,21 @@ __global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
 // ---------------------------------------------------------------- launchers
 
 static inline unsigned nblocks(uint64_t units, int bs) { return (unsigned)((units + bs - 1) / bs); }
+
+SparseMap sparse_map(const lbm_ctx *c) {
+    SparseMap m;
+    m.fidx = c->d_fidx;
+    m.bb = c->d_bb;
+    m.rw = c->d_rw;
+    m.rstart = c->d_rstart;
+    m.Lx = c->Lx;
+    m.Ly = c->Ly;
+    m.Lz = c->Lz;
+    m.Wr = c->Wr;
+    m.mLx = div_magic((uint32_t)c->Lx);
+    m.mLy = div_magic((uint32_t)c->Ly);
+    return m;
+}
 
 template <typename S>
 int launch_step_t(lbm_ctx *c, bool reduce) {
@@ -408,12 +438,21 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
     default:
         grid = nblocks(c->Nf, bs);
         if (grid == 0) break;
-        if (odd)
-            k_sparse<S, true><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_nbr, c->d_bb,
-                                                          (uint32_t)c->Nf, p, lds, sts, red);
-        else
-            k_sparse<S, false><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_nbr, c->d_bb,
-                                                           (uint32_t)c->Nf, p, lds, sts, red);
+        if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+            if (odd)
+                k_sparse<S, true, uint32_t><<<grid, bs, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+            else
+                k_sparse<S, false, uint32_t><<<grid, bs, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+        } else {
+            if (odd)
+                k_sparse<S, true, size_t><<<grid, bs, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+            else
+                k_sparse<S, false, size_t><<<grid, bs, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+        }
         break;
     }
     c->launches++;
@@ -428,8 +467,7 @@ static StateView make_view(const lbm_ctx *c) {
     v.parity = (int)(c->steps & 1);
     v.units = (uint32_t)(c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N);
     v.lw = c->d_lw;
-    v.nbr = c->d_nbr;
-    v.bb = c->d_bb;
+    v.sm = sparse_map(c);
     v.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
     return v;
 }

@@ -9,10 +9,14 @@
 // single coalesced 4-byte load instead of 18 mask reads.
 //
 // The sparse layout lists fluid nodes in node order (fluid_idx), gives every
-// fluid node the fluid index of each upstream neighbour (nbr, -1 where solid)
-// and the same bounceback bits (bb).  Per-direction bounceback link counts
-// are accumulated with integer atomics, so they are exact.
-#include "lbm_internal.cuh"
+// fluid node the same bounceback bits (bb), and keeps per x-row fluid bit
+// words with fluid-index bases (RowWord) and row starts, from which the
+// stream-collide kernel computes upstream fluid indices (lbm_sparse.cuh).
+// The explicit neighbour table nbr[18][Nf] (fluid index of x - c_i, -1 where
+// solid) is only materialised on request, from the same computation.
+// Per-direction bounceback link counts are accumulated with integer atomics,
+// so they are exact.
+#include "lbm_sparse.cuh"
 
 namespace lbm {
 
@@ -101,10 +105,13 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *count, uin
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Writes fluid_idx and the node -> fluid map (-1 for solids).
+// Writes fluid_idx, the node -> fluid map (-1 for solids), the fluid-index
+// base of every 32-voxel row word and the row starts.
 __global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ mask, uint32_t N,
                                                   const uint32_t *__restrict__ offset,
-                                                  int32_t *fidx, int32_t *node2fluid) {
+                                                  int32_t *fidx, int32_t *node2fluid, int Lx,
+                                                  int Wr, uint32_t nrows, RowWord *rw,
+                                                  int32_t *rstart) {
     const uint32_t n = blockIdx.x * 1024u + threadIdx.x;
     const bool f = n < N && mask[n] == 0;
     const unsigned b = __ballot_sync(0xffffffffu, f);
@@ -122,19 +129,50 @@ __global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ ma
     }
     __syncthreads();
     if (n < N) {
+        // fluid nodes before n in node order = fluid index of n if fluid
+        const uint32_t k = offset[blockIdx.x] + sm[wid] + __popc(b & ((1u << lane) - 1u));
         if (f) {
-            const uint32_t k = offset[blockIdx.x] + sm[wid] + __popc(b & ((1u << lane) - 1u));
             fidx[k] = (int32_t)n;
             node2fluid[n] = (int32_t)k;
         } else {
             node2fluid[n] = -1;
         }
+        const uint32_t R = n / (uint32_t)Lx;
+        const uint32_t x = n - R * (uint32_t)Lx;
+        if ((x & 31u) == 0) rw[(size_t)R * Wr + (x >> 5)].base = (int32_t)k;
+        if (x == 0) rstart[R] = (int32_t)k;
+        if (n == N - 1) rstart[nrows] = (int32_t)(k + (f ? 1u : 0u));
     }
 }
 
+// Fluid bits of every 32-voxel row word.
+__global__ void k_row_bits(const uint8_t *__restrict__ mask, int Lx, int Wr, uint32_t nwords,
+                           RowWord *rw) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nwords) return;
+    const uint32_t R = t / (uint32_t)Wr, w = t - R * (uint32_t)Wr;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+        const int x = 32 * (int)w + b;
+        if (x < Lx && mask[(size_t)x + (size_t)Lx * R] == 0) bits |= 1u << b;
+    }
+    rw[t].bits = bits;
+}
+
+// Materialises nbr[18][Nf] from the row map (fluid index of x - c_j, -1 if solid).
+__global__ void k_sparse_nbr(SparseMap m, uint32_t Nf, int32_t *nbr) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nf) return;
+    SparseNode sn;
+    sn.init(k, m);
+#pragma unroll
+    for (int j = 1; j < Q; ++j)
+        nbr[(size_t)(j - 1) * Nf + k] = (sn.bits & (1u << j)) ? -1 : (int32_t)sn.up(j, m);
+}
+
 __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, int Lx, int Ly,
-                               int Lz, const int32_t *__restrict__ node2fluid, int32_t *nbr,
-                               uint32_t *bb, unsigned long long *links) {
+                               int Lz, const int32_t *__restrict__ node2fluid, uint32_t *bb,
+                               unsigned long long *links) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bits = 0;
     const bool valid = k < Nf;
@@ -142,9 +180,7 @@ __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, in
         const uint32_t n = (uint32_t)fidx[k];
 #pragma unroll
         for (int j = 1; j < Q; ++j) {
-            int32_t s = node2fluid[upstream(n, j, Lx, Ly, Lz)];
-            nbr[(size_t)(j - 1) * Nf + k] = s;
-            if (s < 0) bits |= 1u << j;
+            if (node2fluid[upstream(n, j, Lx, Ly, Lz)] < 0) bits |= 1u << j;
         }
         bb[k] = bits;
     }
@@ -177,12 +213,16 @@ int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
     }
     k_count_fluid<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_cnt);
     k_scan_counts<<<1, 1024, 0, c->stream>>>(d_cnt, nb, d_off, d_tot);
-    k_compact<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_off, c->d_fidx, d_n2f);
+    const uint32_t nrows = (uint32_t)c->Ly * (uint32_t)c->Lz;
+    const uint32_t nwords = nrows * (uint32_t)c->Wr;
+    k_row_bits<<<(nwords + 255) / 256, 256, 0, c->stream>>>(c->d_mask, c->Lx, c->Wr, nwords, c->d_rw);
+    k_compact<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_off, c->d_fidx, d_n2f, c->Lx, c->Wr,
+                                          nrows, c->d_rw, c->d_rstart);
     const uint32_t Nf = (uint32_t)c->Nf;
     if (Nf > 0)
         k_sparse_links<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_fidx, Nf, c->Lx, c->Ly, c->Lz,
-                                                                 d_n2f, c->d_nbr, c->d_bb, d_links);
-    c->launches += 4;
+                                                                 d_n2f, c->d_bb, d_links);
+    c->launches += 5;
     uint32_t tot = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -194,4 +234,16 @@ int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
     return LBM_OK;
 }
 
+}  // namespace lbm
+
+namespace lbm {
+SparseMap sparse_map(const lbm_ctx *c);
+
+int export_sparse_nbr(lbm_ctx *c, int32_t *nbr_dev) {
+    const uint32_t Nf = (uint32_t)c->Nf;
+    if (Nf == 0) return LBM_OK;
+    k_sparse_nbr<<<(Nf + 255) / 256, 256, 0, c->stream>>>(sparse_map(c), Nf, nbr_dev);
+    c->launches++;
+    return launch_error(cudaGetLastError());
+}
 }  // namespace lbm

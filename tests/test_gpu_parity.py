@@ -73,14 +73,18 @@ def test_fp64_steps_match_oracle(L, ora, geom, layout, st, lam, linear):
     O = ora.Solver(mask, ora.rates(st, tau, lam), F3, linear=linear)
     O.set_f(f0)
     assert dev_err(S.get_populations(), O.get_f()) <= 1e-15
+    # The oracle carries unshifted f (up to 1/3, rounding 3.7e-17 per
+    # operation) while these random states deviate by ~1e-3 from rest, so one
+    # oracle rounding is ~1e-14 of the deviation scale; ~100 dependent
+    # operations per update over <= 7 steps bound the gap by 1e-11.
     for n in (6, 1):  # compare after an even and an odd number of steps
         S.step(n)
         O.step(n)
-        assert dev_err(S.get_populations(), O.get_f()) <= 1e-12
+        assert dev_err(S.get_populations(), O.get_f()) <= 1e-11
         ug, uo = S.velocity(), O.velocity()
-        assert np.abs(ug - uo).max() <= 1e-12 * np.abs(uo).max()
+        assert np.abs(ug - uo).max() <= 1e-11 * np.abs(uo).max()
         Ug, Uo = S.mean_velocity(), O.mean_velocity()
-        assert np.abs(Ug - Uo).max() <= 1e-12 * np.abs(Uo).max()
+        assert np.abs(Ug - Uo).max() <= 1e-11 * np.abs(Uo).max()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -127,7 +131,11 @@ def test_config1_fp64_permeability(L, config1, layout):
     k = S.permeability()[0]
     assert abs(k - k_ora) <= 1e-10 * abs(k_ora)
     u = S.velocity()
-    assert np.abs(u - u_ora).max() <= 1e-12 * np.abs(u_ora).max()
+    # 1e-12 relative, plus the oracle's own rounding floor: it stores
+    # unshifted f (<= 1/3, 3.7e-17 per rounding) and sums ten of them for a
+    # velocity component, ~4e-16 absolute (3.8e-16 measured here, where
+    # |u| <= 3.6e-4); the GPU stores deviations from rest and is finer.
+    assert np.abs(u - u_ora).max() <= 1e-12 * np.abs(u_ora).max() + 1e-15
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -201,7 +209,7 @@ def test_degenerate_lattices(L, ora, layout):
         O = ora.Solver(mask, ora.rates("D", 0.9), F3)
         S.step(9)
         O.step(9)
-        assert dev_err(S.get_populations(), O.get_f()) <= 1e-12
+        assert dev_err(S.get_populations(), O.get_f()) <= 1e-11
 
 
 def test_unstable_is_reported(L, geom):
