@@ -84,6 +84,9 @@ def lib():
         L.ora_run_to_convergence.restype = C.c_int
         L.ora_set_threads.argtypes = [C.c_int]
         L.ora_get_threads.restype = C.c_int
+        L.ora_run_to_convergence_rule.argtypes = [C.c_void_p, C.c_double, C.c_int64, C.c_int64,
+                                                  C.c_int, C.POINTER(C.c_int64), dp]
+        L.ora_run_to_convergence_rule.restype = C.c_int
         L.ora_rates_magic.argtypes = [C.c_double, C.c_double, C.c_double, dp]
         L.ora_rates_magic.restype = C.c_int
         L.ora_stream_field.argtypes = [C.c_void_p, dp, dp]
@@ -232,11 +235,13 @@ class Solver:
     def steps(self) -> int:
         return int(lib().ora_steps_done(self._h))
 
-    def run_to_convergence(self, tol: float, K: int = 1, max_steps: int = 10**6):
+    def run_to_convergence(self, tol: float, K: int = 1, max_steps: int = 10**6, rule: int = 0):
+        """Stopping rule of eq. (convergence); rule 1 applies it to the mean
+        over two consecutive steps.  Returns (rc, steps, U stopped on)."""
         steps = C.c_int64(0)
         U = np.zeros(3)
-        rc = lib().ora_run_to_convergence(self._h, float(tol), int(K), int(max_steps),
-                                          C.byref(steps), U)
+        rc = lib().ora_run_to_convergence_rule(self._h, float(tol), int(K), int(max_steps),
+                                               int(rule), C.byref(steps), U)
         return rc, int(steps.value), U
 
     def stream_field(self, f: np.ndarray) -> np.ndarray:

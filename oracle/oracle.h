@@ -70,6 +70,12 @@ int64_t ora_steps_done(ora_solver *h);
  * converged, 2 non-finite. */
 int ora_run_to_convergence(ora_solver *h, double tol, int64_t K, int64_t max_steps,
                            int64_t *steps, double U[3]);
+/* The same with a choice of stopping rule: rule 0 is the rule above; rule 1
+ * applies it to the mean over two consecutive steps, measured in the last
+ * three steps of a chunk (K >= 3): Ubar_b = (U_b + U_c)/2 against
+ * Ubar_a = (U_a + U_b)/2.  U receives the measure the rule stopped on. */
+int ora_run_to_convergence_rule(ora_solver *h, double tol, int64_t K, int64_t max_steps,
+                                int rule, int64_t *steps, double U[3]);
 void ora_set_threads(int n);
 int ora_get_threads(void);
 
@@ -90,7 +96,12 @@ void ora_adjoint_apply(ora_solver *h, const double *in, double *out);
 
 /* Steady fixed-point adjoint of k along the drive (largest |F_j|):
  * psi = J_C^T S^T psi + dk/dh, iterated from psi = dk/dh until the largest
- * change is <= tol times the largest |psi| (checked every K iterations).
+ * change over two iterations is <= tol times the largest |psi| (checked every
+ * K iterations).  The linearisation point h is the mean of the streamed
+ * states of the current and the next step (the solver advances one step),
+ * and the gradient uses the mean of the last two iterates: both means remove
+ * the period-2 component that bounceback in thin gaps can leave in either
+ * iteration.
  * The gradient is dk/dtheta = dJ/dtheta + (S^T psi) . dC/dtheta.
  * (set, tau, Lambda) must be the parameters the solver's rates came from.
  * grad = {dk/dtau, dk/dLambda, dk/dLambda_q, dk/dLambda_m, dk/dF_x,
