@@ -48,6 +48,13 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the other-layout and permeability-error legs")
+    p.add_argument("--sweep", default="subset", choices=["none", "subset", "full"],
+                   help="batched parameter sweep vs the same lattices one by one")
+    p.add_argument("--adjoint", action="store_true", default=True)
+    p.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    p.add_argument("--large", action="store_true", default=True,
+                   help="1024^3 low-porosity sparse leg, FP32 vs FP16 storage")
+    p.add_argument("--no-large", dest="large", action="store_false")
     return p.parse_args()
 
 
@@ -338,6 +345,13 @@ def run_ours(args):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_run(mask, args, stream)
 
+    if rank == 0 and args.sweep != "none":
+        out["sweep"] = sweep_run(args, stream)
+    if rank == 0 and args.adjoint:
+        out["adjoint"] = adjoint_run(args, stream)
+    if rank == 0 and args.large:
+        out["large"] = large_run(args, stream)
+
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, text = oracle_sample(mask)
         out["cpu_baseline"] = {"value": v, "unit": "fluid MLUPS", "cores": cores,
@@ -391,6 +405,146 @@ def e2e_run(mask, args, stream):
             "wall_s": t1 - t0, "permeability_lu": float(k[0]),
             "includes": "lbm_create (mask upload, link tables, allocation), the production "
                         "loop, lbm_permeability"}
+
+
+SWEEP_TAUS = (0.6, 0.8, 1.0, 1.15, 1.3, 1.6, 2.0)
+SWEEP_SETS = (("A", 3 / 16), ("B", 3 / 16), ("C", 3 / 16), ("D", 3 / 16), ("E", 1 / 64),
+              ("E", 3 / 16), ("E", 3 / 8))
+
+
+def sweep_lattices(kind):
+    """The parameter study of Secs. 4.1-4.3 on sphere arrays: SC/BCC/FCC cells
+    at solid fractions 0.1-0.5 and edges 16/32/64/96 x Sets A-E x 7 taus
+    ("full", 2940 lattices), or a seeded subset of it (edges 16/32, three
+    fractions, three taus, all seven rate sets: 378 lattices)."""
+    from paper_1902_11193_gb300 import geometry
+
+    if kind == "full":
+        edges, fracs, taus = (16, 32, 64, 96), (0.1, 0.2, 0.3, 0.4, 0.5), SWEEP_TAUS
+    else:
+        edges, fracs, taus = (16, 32), (0.1, 0.3, 0.5), (0.6, 1.0, 1.6)
+    lats = []
+    for arr in ("sc", "bcc", "fcc"):
+        for L in edges:
+            for c in fracs:
+                m = geometry.sphere_array(L, arr, c=c)
+                for st, lam in SWEEP_SETS:
+                    for tau in taus:
+                        lats.append(dict(mask=m, set_=st, tau=tau, Lambda=lam,
+                                         force=(1e-6, 0.0, 0.0)))
+    return lats
+
+
+def sweep_run(args, stream):
+    """Converges every lattice of the sweep (paper's rule, tol 1e-6 on k) in
+    one batch, then the same lattices one by one through lbm_run_to_convergence;
+    wall time of each, launches of each."""
+    import torch
+
+    from paper_1902_11193_gb300 import lbm
+
+    lats = sweep_lattices(args.sweep)
+    K = 100
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = lbm.LBMBatch(lats, precision="fp32", check_interval=K, max_steps=200000, stream=stream)
+    t1 = time.perf_counter()
+    steps, status = B.run(1e-6)
+    kb = B.permeability()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    lay, npt = B.config()
+    blaunch = B.kernel_launches
+    B.close()
+    t3 = time.perf_counter()
+    ks, seq_launches, seq_steps = [], 0, []
+    for l, layout in zip(lats, lay):
+        S = lbm.LBMSolver(l["mask"], l["set_"], l["tau"], l["Lambda"], l["force"],
+                          precision="fp32", layout=["ab", "aa", "sparse"][layout],
+                          check_interval=K, max_steps=200000, stream=stream)
+        rc, st = S.run_to_convergence(1e-6)
+        ks.append(S.permeability())
+        seq_launches += S.kernel_launches
+        seq_steps.append(st)
+        S.close()
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    fluid = np.array([int((l["mask"] == 0).sum()) for l in lats])
+    updates = float(np.sum(fluid * steps))
+    return {"lattices": len(lats), "kind": args.sweep, "tol": 1e-6, "check_interval": K,
+            "converged": int(np.sum(status == 0)), "steps_total": int(steps.sum()),
+            "batched_s": t2 - t1, "batched_setup_s": t1 - t0, "sequential_s": t4 - t3,
+            "speedup": (t4 - t3) / (t2 - t1),
+            "batched_fluid_MLUPS": updates / (t2 - t1) / 1e6,
+            "sequential_fluid_MLUPS": float(np.sum(fluid * np.array(seq_steps))) / (t4 - t3) / 1e6,
+            "batched_launches": blaunch, "sequential_launches": seq_launches,
+            "same_steps": bool(np.array_equal(steps, np.array(seq_steps))),
+            "max_k_diff": float(np.max(np.abs(np.array(ks) - kb))),
+            "layouts": {"aa": int(np.sum(lay == 1)), "sparse": int(np.sum(lay == 2)),
+                        "npt2": int(np.sum(npt == 2))}}
+
+
+def adjoint_run(args, stream):
+    """Steady adjoint on the 128^3 Boolean medium (r = 6, porosity 0.35):
+    FP32 forward to the paper's rule, then lbm_adjoint; gradients normalised."""
+    import torch
+
+    from paper_1902_11193_gb300 import geometry, lbm
+
+    mask, _ = geometry.boolean(128, 6, 0.35, seed=1902_11193 + 4)
+    res = {"workload": "boolean-128^3 r=6 porosity=0.35, Set D tau=1, F=1e-6, fp32 sparse"}
+    S = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision="fp32", layout="sparse",
+                      check_interval=100, stream=stream)
+    t0 = time.perf_counter()
+    rc, steps = S.run_to_convergence(1e-9)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = S.adjoint(1e-7)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    k = g["k"]
+    nf = int((mask == 0).sum())
+    res.update({"forward_steps": steps, "forward_s": t1 - t0, "adjoint_iterations": g["iterations"],
+                "adjoint_s": t2 - t1, "adjoint_residual": g["residual"],
+                "adjoint_fluid_MLUPS": nf * g["iterations"] / (t2 - t1) / 1e6,
+                "k": k, "tau_dk_dtau_over_k": g["dtau"] * 1.0 / k,
+                "Lq_dk_dLq_over_k": g["dLambda_q"] * (3 / 16) / k,
+                "Lm_dk_dLm_over_k": g["dLambda_m"] * (3 / 8) / k,
+                "F_dk_dF_over_k": g["dF"][0] * 1e-6 / k})
+    S.close()
+    return res
+
+
+def large_run(args, stream):
+    """1024^3 Boolean medium (r = 8, porosity 0.20), Set D, tau = 1, sparse
+    layout: FP32 vs FP16 storage (FP32 arithmetic), per-launch timing of 40
+    steps after warm-up, and the relative difference of the mean velocity
+    between the two storages after the same number of steps."""
+    import torch
+
+    from paper_1902_11193_gb300 import geometry, lbm
+
+    t0 = time.perf_counter()
+    mask, ns = geometry.boolean(1024, 8, 0.20, seed=1902_11193 + 5)
+    tgen = time.perf_counter() - t0
+    nf = int((mask == 0).sum())
+    res = {"workload": "boolean-1024^3 r=8 porosity=0.20, Set D tau=1, F=1e-6, sparse",
+           "fluid_nodes": nf, "spheres": ns, "mask_gen_s": tgen}
+    U = {}
+    peak, _ = load_peaks()
+    for prec in ("fp32", "fp16"):
+        S = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision=prec, layout="sparse",
+                          stream=stream)
+        S.step(10)
+        kmean, kmin = time_kernel_launches(S, 40, stream)
+        U[prec] = S.mean_velocity()[0]
+        mlups = nf / (kmean * 1e-3) / 1e6
+        res[prec] = {"fluid_MLUPS": mlups, "launch_ms_mean": kmean,
+                     "hbm_frac_algorithmic": BYTES_PER_UPDATE[prec] * nf / (kmean * 1e-3) / 1e9 / peak}
+        S.close()
+        torch.cuda.synchronize()
+    res["fp16_vs_fp32_mean_velocity_rel_diff_after_50_steps"] = abs(U["fp16"] - U["fp32"]) / abs(U["fp32"])
+    return res
 
 
 def main():

@@ -78,6 +78,13 @@ typedef struct {
     int32_t fp16_scale_log2;  /* S for FP16 storage; 0 selects it from the drive */
     int32_t block_size;       /* threads per block of the stream-collide kernel;
                                  0 = default (256) */
+    int32_t stop_rule;        /* 0 (default): eq. (convergence) on the per-step value;
+                                 1: on the mean over two consecutive steps, measured
+                                 in the last three steps of a chunk (K >= 3).  Halfway
+                                 bounceback in gaps one or two voxels wide supports
+                                 modes of eigenvalue near -1 that keep the per-step
+                                 value alternating around the fixed point; the
+                                 two-step mean cancels them. */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -122,6 +129,12 @@ int lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t *steps_taken);
 /* Mean velocity U[3] of the current state after streaming (not advanced). */
 int lbm_mean_velocity(lbm_ctx *ctx, double U[3]);
 
+/* The mean velocity the last lbm_run_to_convergence stopped on (the last
+ * measured step under stop_rule 0, the two-step mean under stop_rule 1) and
+ * the permeability from it (eq. perm_calc).  LBM_ENOSTATE before a run. */
+int lbm_converged_velocity(lbm_ctx *ctx, double U[3]);
+int lbm_converged_permeability(lbm_ctx *ctx, double k[3]);
+
 /* eq. (perm_calc) with body forcing: k_j = nu <u_j> / F_j, nu = (tau-1/2)/3,
  * NaN where F_j == 0 (lattice units). */
 int lbm_permeability(lbm_ctx *ctx, double k[3]);
@@ -159,6 +172,100 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  * (same stream if opt is NULL: a fresh one).  Resuming continues bit-identically. */
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt);
+
+/* Gradient of the converged permeability k along the drive direction d (the
+ * largest |F_j|), from lbm_adjoint. */
+typedef struct {
+    double dk_dtau;      /* total derivative in tau under the set's rate rules
+                            (rates given directly: through s_nu = 1/tau only) */
+    double dk_dLambda;   /* Sets B, D, E: both odd rates through their magic
+                            parameters moved together (eq. Magic param); NaN otherwise */
+    double dk_dLambda_q; /* Sets B, D, E: through s_q alone; NaN otherwise */
+    double dk_dLambda_m; /* Sets B, D, E: through s_m alone; NaN otherwise */
+    double dk_dF[3];     /* with respect to the body-force components */
+    double dk_ds[6];     /* partial derivatives with respect to the grouped rates
+                            (s_e, s_eps, s_q, s_nu, s_pi, s_m), tau fixed in nu */
+    double k;            /* k_d at the state the adjoint was taken */
+    int64_t iterations;  /* adjoint iterations run */
+    double residual;     /* final ||psi_{n+1} - psi_n|| / ||psi_{n+1}|| */
+} lbm_grad;
+
+/* Steady fixed-point adjoint of k_d (no counterpart in the paper: the
+ * derivative of eq. (perm_calc) at a converged state).  Solves
+ * psi = J_C^T S^T psi + dk/dh in the context's precision (FP64 for FP64
+ * storage, FP32 otherwise) with the residual checked every check_interval
+ * iterations until <= tol or max_iter, then reduces the gradient in FP64.
+ * The state must be the converged one: LBM_ENOSTATE unless the last
+ * lbm_run_to_convergence succeeded and nothing stepped or set the state
+ * since.  The linearisation point is the mean of the streamed states of the
+ * current and the next step (the context advances one step), the residual
+ * compares iterates two apart and the gradient uses the mean of the last two
+ * iterates, so a period-2 component of either iteration drops out.
+ * LBM_EINVAL if every force component is zero.  Allocates four
+ * population-sized work arrays for the duration of the call. */
+int lbm_adjoint(lbm_ctx *ctx, double tol, int64_t max_iter, lbm_grad *out);
+
+/* ------------------------------------------------------------------------
+ * Batched sweep: many lattices of uneven sizes stepped together, as in the
+ * paper's parameter study (Sets A-E x tau x geometry x resolution, Secs.
+ * 4.1-4.3).  One persistent cooperative kernel per chunk of check_interval
+ * steps walks a tile table of every active lattice, with a bounded-wait grid
+ * barrier between steps; each lattice measures its mean velocity in the
+ * chunk's last two steps and retires when its own stopping rule holds.  The
+ * chunk (kernel, per-lattice reductions, result copy) is replayed from a
+ * CUDA graph.  Each lattice's layout (dense AA or sparse) and nodes per
+ * thread are chosen by timing candidates per distinct image (autotuner), or
+ * fixed by the options. */
+
+typedef struct {
+    const uint8_t *mask;  /* host, Lz*Ly*Lx, 1 = solid (copied at create) */
+    int32_t dims[3];
+    int32_t set;          /* lbm_set; -1: rates from s[] */
+    double tau, Lambda;
+    double s[19];         /* used when set == -1 */
+    double force[3];
+} lbm_lattice_desc;
+
+typedef struct {
+    int32_t precision;          /* LBM_FP32_SHIFTED (default) or LBM_FP64 */
+    int32_t layout;             /* -1 (default): autotune; LBM_LAYOUT_AA or LBM_LAYOUT_SPARSE */
+    int32_t nodes_per_thread;   /* 0 (default): autotune; 1 or 2 */
+    int32_t check_interval;     /* K >= 2, default 100 */
+    int32_t linear_eq;
+    int64_t max_steps;          /* per lattice, default 1000000 */
+    void *cuda_stream;          /* NULL: the batch makes one */
+    int32_t use_graph;          /* 1 (default): replay chunks from a CUDA graph */
+    int32_t barrier_timeout_ms; /* bounded grid-barrier wait, default 2000 */
+    int32_t test_skip_block;    /* test hook, default -1: block that skips its first barrier
+                                   arrival, so the others' waits run out (LBM_ETIMEOUT) */
+    int32_t stop_rule;          /* as lbm_options.stop_rule */
+} lbm_batch_options;
+
+typedef struct lbm_batch lbm_batch;
+
+void lbm_batch_default_options(lbm_batch_options *opt);
+/* Creates n lattices (each validated like lbm_create).  Errors as lbm_create. */
+int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *lattices,
+                     const lbm_batch_options *opt);
+/* Runs every lattice until its stopping rule (as lbm_run_to_convergence, with
+ * the batch's check_interval) holds or it reaches max_steps.  steps[n] and
+ * status[n] (nullable) receive each lattice's step count and result
+ * (0, LBM_ENOTCONV or LBM_EUNSTABLE).  Returns LBM_ETIMEOUT if a grid-barrier
+ * wait expired (the batch is then unusable), else 0. */
+int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status);
+/* Per-lattice results: k[n][3] (eq. perm_calc) from the mean velocity each
+ * lattice's stopping rule stopped on (the current state's before a run), and
+ * the current states' mean velocities U[n][3]. */
+int lbm_batch_permeability(lbm_batch *b, double *k);
+int lbm_batch_mean_velocity(lbm_batch *b, double *U);
+/* Layout and nodes per thread chosen for each lattice (nullable outputs). */
+int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *nodes_per_thread);
+/* The context of lattice i (owned by the batch; valid until lbm_batch_destroy),
+ * for the single-lattice readers (populations, velocity, checkpoint). */
+lbm_ctx *lbm_batch_lattice(lbm_batch *b, int32_t i);
+/* Persistent-kernel launches and graph replays so far (launch accounting). */
+int64_t lbm_batch_kernel_launches(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
 
 /* Number of CUDA kernels this context has launched (for launch accounting). */
 int64_t lbm_kernel_launches(const lbm_ctx *ctx);

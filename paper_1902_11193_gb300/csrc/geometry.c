@@ -17,6 +17,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define GEOM_OK 0
@@ -135,6 +136,71 @@ int geom_boolean(uint8_t *mask, int Lx, int Ly, int Lz, double r, double phi_tar
     if (n_spheres) *n_spheres = ns;
     if (n_solid) *n_solid = solid;
     return GEOM_OK;
+}
+
+/* Union-find root with path halving. */
+static int32_t uf_find(int32_t *p, int32_t a) {
+    while (p[a] != a) {
+        p[a] = p[p[a]];
+        a = p[a];
+    }
+    return a;
+}
+
+/* Fills as solid every fluid cluster that is not the largest one, where two
+ * fluid voxels belong to one cluster when a D3Q19 link (the 6 face and 12
+ * edge neighbours, periodic wrap) joins them.  Enclosed pores carry no
+ * steady flow; left in, a fully enclosed voxel under halfway bounceback keeps
+ * a momentum mode that flips sign every step and never decays.  Returns the
+ * number of voxels filled, or -1 on bad arguments / allocation failure. */
+int64_t geom_fill_isolated(uint8_t *mask, int Lx, int Ly, int Lz) {
+    if (!mask || Lx <= 0 || Ly <= 0 || Lz <= 0) return -1;
+    const int64_t N = (int64_t)Lx * Ly * Lz;
+    if (N >= ((int64_t)1 << 31)) return -1;
+    int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!par) return -1;
+    for (int64_t n = 0; n < N; ++n) par[n] = (int32_t)n;
+    /* half of the 18 links suffice: the other half are their opposites */
+    static const int L9[9][3] = {{1, 0, 0},  {0, 1, 0}, {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                 {1, 0, 1},  {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                const int64_t n = x + (int64_t)Lx * (y + (int64_t)Ly * z);
+                if (mask[n]) continue;
+                for (int k = 0; k < 9; ++k) {
+                    const int xn = wrap((long)x + L9[k][0], Lx), yn = wrap((long)y + L9[k][1], Ly),
+                              zn = wrap((long)z + L9[k][2], Lz);
+                    const int64_t m = xn + (int64_t)Lx * (yn + (int64_t)Ly * zn);
+                    if (mask[m]) continue;
+                    const int32_t a = uf_find(par, (int32_t)n), b = uf_find(par, (int32_t)m);
+                    if (a != b) par[a > b ? a : b] = a < b ? a : b;
+                }
+            }
+    /* cluster sizes at the roots, then the largest */
+    int32_t *size = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    if (!size) {
+        free(par);
+        return -1;
+    }
+    int32_t best = -1, bestn = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        if (mask[n]) continue;
+        const int32_t r = uf_find(par, (int32_t)n);
+        if (++size[r] > bestn || (size[r] == bestn && r < best)) {
+            bestn = size[r];
+            best = r;
+        }
+    }
+    int64_t filled = 0;
+    for (int64_t n = 0; n < N; ++n)
+        if (!mask[n] && uf_find(par, (int32_t)n) != best) {
+            mask[n] = 1;
+            ++filled;
+        }
+    free(size);
+    free(par);
+    return filled;
 }
 
 /* Plane slit: H fluid layers (y = 0..H-1) and W solid layers (y = H..H+W-1),

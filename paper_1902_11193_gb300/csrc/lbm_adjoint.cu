@@ -1,0 +1,435 @@
+// Steady fixed-point adjoint of the permeability (no counterpart in the
+// paper's method; it differentiates the converged k of eq. perm_calc with
+// respect to tau, the magic parameters and the body force).
+//
+// In the streamed variable h = S f* one time step is h -> S C(h).  At the
+// steady state the adjoint psi of J = k along the drive d solves
+//     psi = J_C(h)^T S^T psi + dJ/dh,      dJ/dh_i = nu c_{i,d} / (F_d N),
+// and dk/dtheta = dJ/dtheta + (S^T psi) . dC/dtheta.
+//  S^T     transposed streaming: the post-collision population i of x went
+//          to x + c_i, or, where that voxel is solid, back into slot opp(i)
+//          of x (the reversed bounceback link).
+//  J_C^T   with C = M^-1 [m - S (m - m^eq) + (I - S/2) m^F], M^-1 = M^T D^-1:
+//          J_C^T phi = M^T A^T D^-1 M phi with
+//          A = I - S + S dm^eq/dm + (I - S/2) dm^F/dm.  m^eq and m^F depend on
+//          m only through rho and j, so A^T relaxes every non-conserved moment
+//          by (1 - s_k) and adds to the rho and j rows the sums over the
+//          moments' equilibrium and forcing derivatives.
+// The iteration converges at the rate of the forward problem.  Halfway
+// bounceback in gaps one or two voxels wide gives both the forward step and
+// this iteration modes of eigenvalue near -1, so the linearisation point is
+// the mean of two consecutive streamed states, the residual compares
+// iterates two apart (||psi_{n+1} - psi_{n-1}|| / ||psi_{n+1}||, reduced in
+// FP64 every K steps) and the gradient uses the mean of the last two iterates.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+// Same unit machinery as the state readers (lbm_kernels.cu).
+struct AdjView {
+    int layout;
+    uint32_t units;
+    const uint32_t *lw;
+    SparseMap sm;
+    Dims d;
+};
+
+struct AdjUnit {
+    DenseNode d;
+    SparseNode s;
+    uint32_t bits;  // bit j: x - c_j is solid
+    bool fluid;
+    __device__ __forceinline__ void init(uint32_t u, const AdjView &v) {
+        if (v.layout == LBM_LAYOUT_SPARSE) {
+            s.init(u, v.sm);
+            bits = s.bits;
+            fluid = true;
+        } else {
+            bits = v.lw[u];
+            fluid = !(bits & SOLID_BIT);
+            if (fluid) d.init(u, v.d);
+        }
+    }
+    // unit index of the upstream voxel x - c_j (valid where bit j is clear)
+    __device__ __forceinline__ uint32_t up(int j, uint32_t u, const AdjView &v) const {
+        return v.layout == LBM_LAYOUT_SPARSE ? s.up(j, v.sm) : d.up(j);
+    }
+};
+
+// Where the streamed population i of unit u is kept by the current state
+// (the same rule as the forward readers; duplicated here so the adjoint
+// translation unit stands alone).
+struct AdjState {
+    int layout, parity;
+};
+
+__device__ __forceinline__ size_t streamed_loc(const AdjState &st, const AdjView &v, uint32_t u,
+                                               int j, const AdjUnit &un) {
+    if (st.layout == LBM_LAYOUT_AB) {
+        if (j == 0) return u;
+        if (un.bits & (1u << j)) return (size_t)opp(j) * v.units + u;
+        return (size_t)j * v.units + un.up(j, u, v);
+    }
+    if (st.parity == 0 || j == 0 || (un.bits & (1u << j))) return (size_t)j * v.units + u;
+    return (size_t)opp(j) * v.units + un.up(j, u, v);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double v[NV], double *partials) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+    __shared__ double sm[32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) sm[wid][a] = v[a];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double acc = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) acc += sm[w][threadIdx.x];
+        partials[(size_t)NV * blockIdx.x + threadIdx.x] = acc;
+    }
+}
+
+// Sum_k w_k dP_k/dv_a over the moments whose equilibrium (v = j), forcing
+// (v = F for d/du, v = u for d/dF) depends quadratically on the drive:
+// the derivative of (38 v.X, -11 v.X, 2(2 vx Xx - vy Xy - vz Xz), -m9/2,
+// 2(vy Xy - vz Xz), -m11/2, vx Xy + vy Xx, vy Xz + vz Xy, vx Xz + vz Xx)
+// with respect to X_a, contracted with w.
+template <typename T>
+__device__ __forceinline__ T dotP(int a, T vx, T vy, T vz, const T w[Q]) {
+    if (a == 0)
+        return T(38) * vx * w[1] - T(11) * vx * w[2] + T(4) * vx * w[9] - T(2) * vx * w[10] +
+               vy * w[13] + vz * w[15];
+    if (a == 1)
+        return T(38) * vy * w[1] - T(11) * vy * w[2] - T(2) * vy * w[9] + vy * w[10] +
+               T(2) * vy * w[11] - vy * w[12] + vx * w[13] + vz * w[14];
+    return T(38) * vz * w[1] - T(11) * vz * w[2] - T(2) * vz * w[9] + vz * w[10] -
+           T(2) * vz * w[11] + vz * w[12] + vy * w[14] + vx * w[15];
+}
+
+// phi: the transposed-streamed adjoint at one node; h: the steady streamed
+// populations there.  Returns b = D^-1 M phi and the shifted momentum of h.
+template <typename T>
+__device__ __forceinline__ void adj_moments(const T phi[Q], const T h[Q], const Collide<T> &p,
+                                            T b[Q], T &jx, T &jy, T &jz) {
+    T a[Q];
+    moments_of<T>(phi, a);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) b[k] = a[k] * inv_norm<T>(k);
+    jx = h[1] - h[2] + h[7] - h[8] + h[9] - h[10] + h[11] - h[12] + h[13] - h[14] + T(0.5) * p.Fx;
+    jy = h[3] - h[4] + h[7] - h[8] - h[9] + h[10] + h[15] - h[16] + h[17] - h[18] + T(0.5) * p.Fy;
+    jz = h[5] - h[6] + h[11] - h[12] - h[13] + h[14] + h[15] - h[16] - h[17] + h[18] + T(0.5) * p.Fz;
+}
+
+// H = streamed state (average = 0) or H = (H + streamed state) / 2 (average = 1).
+template <typename S>
+__global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjState st,
+                                                     float ld_scale, typename Store<S>::C *H,
+                                                     int average) {
+    using C = typename Store<S>::C;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= v.units) return;
+    AdjUnit un;
+    un.init(u, v);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const C val = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
+        C *dst = H + (size_t)i * v.units + u;
+        *dst = average ? C(0.5) * (*dst + val) : val;
+    }
+}
+
+// psi_out = J_C(h)^T S^T psi_in + coef c_{., d}.  psi_out holds the iterate
+// before psi_in on entry; with `partials`, also the block sums of
+// |new - that iterate|^2 (a change over two iterations, blind to a period-2
+// component) and |new|^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in,
+                                                  T *__restrict__ psi_out, AdjView v, Collide<T> p,
+                                                  T coef, int d, double *partials) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    double r[2] = {0.0, 0.0};
+    if (u < v.units) {
+        AdjUnit un;
+        un.init(u, v);
+        if (un.fluid) {
+            T phi[Q], h[Q], b[Q], c[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                // population i of x went downstream to x + c_i = x - c_opp(i)
+                const int o = opp(i);
+                phi[i] = (i == 0 || (un.bits & (1u << o)))
+                             ? psi_in[(size_t)(i == 0 ? 0 : o) * v.units + u]
+                             : psi_in[(size_t)i * v.units + un.up(o, u, v)];
+                h[i] = H[(size_t)i * v.units + u];
+            }
+            T jx, jy, jz;
+            adj_moments<T>(phi, h, p, b, jx, jy, jz);
+            const T q = p.linear ? T(0) : T(1);
+            T sb[Q], kb[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const T s = rate_of<T>(k, p);
+                sb[k] = s * b[k];
+                kb[k] = (T(1) - T(0.5) * s) * b[k];
+                c[k] = (T(1) - s) * b[k];
+            }
+            c[0] = b[0] - T(11) * sb[1] + T(3) * sb[2];
+            c[3] = b[3] - T(2.0 / 3.0) * sb[4] + q * (dotP<T>(0, jx, jy, jz, sb) + dotP<T>(0, p.Fx, p.Fy, p.Fz, kb));
+            c[5] = b[5] - T(2.0 / 3.0) * sb[6] + q * (dotP<T>(1, jx, jy, jz, sb) + dotP<T>(1, p.Fx, p.Fy, p.Fz, kb));
+            c[7] = b[7] - T(2.0 / 3.0) * sb[8] + q * (dotP<T>(2, jx, jy, jz, sb) + dotP<T>(2, p.Fx, p.Fy, p.Fz, kb));
+            T out[Q];
+            populations_from<T>(c, out);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ci = d == 0 ? cx(i) : (d == 1 ? cy(i) : cz(i));
+                const T val = out[i] + coef * T(ci);
+                T *dst = psi_out + (size_t)i * v.units + u;
+                if (partials) {
+                    const double dv = (double)val - (double)*dst;
+                    r[0] += dv * dv;
+                    r[1] += (double)val * (double)val;
+                }
+                *dst = val;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) psi_out[(size_t)i * v.units + u] = T(0);
+        }
+    }
+    if (partials) block_sum_store<2>(r, partials);
+}
+
+// Per-node gradient contributions at the converged adjoint, with psi the
+// mean of the last two iterates (psi_a + psi_b) / 2:
+// [0..5] dk/ds for the rate groups (e, eps, q, nu, pi, m):
+//        sum_k b_k (-(m_k - meq_k) - mF_k / 2) over the group's moments;
+// [6..8] dk/dF_a through the collision:
+//        b_{j_a} - (2/3) b_{q_a} + q [ (1/2) dP_a(j; s b) + dP_a(j + F/2; (1 - s/2) b) ];
+// [9]    the drive component of sum_x (sum_i c_i h_i + F/2) (N times the mean
+//        velocity of the linearisation point).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const T *__restrict__ psi_a,
+                                                  const T *__restrict__ psi_b, AdjView v,
+                                                  Collide<T> p, int d, double *partials) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    double gsum[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (u < v.units) {
+        AdjUnit un;
+        un.init(u, v);
+        if (un.fluid) {
+            T phi[Q], h[Q], b[Q], m[Q], meq[Q], mF[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int o = opp(i);
+                const size_t at = (i == 0 || (un.bits & (1u << o)))
+                                      ? (size_t)(i == 0 ? 0 : o) * v.units + u
+                                      : (size_t)i * v.units + un.up(o, u, v);
+                phi[i] = T(0.5) * (psi_a[at] + psi_b[at]);
+                h[i] = H[(size_t)i * v.units + u];
+            }
+            T jx, jy, jz;
+            adj_moments<T>(phi, h, p, b, jx, jy, jz);
+            moments_of<T>(h, m);
+            eq_and_force<T>(m[0], jx, jy, jz, p, meq, mF);
+            double rk[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                rk[k] = (double)b[k] * (-((double)m[k] - (double)meq[k]) - 0.5 * (double)mF[k]);
+            gsum[0] = rk[1];
+            gsum[1] = rk[2];
+            gsum[2] = rk[4] + rk[6] + rk[8];
+            gsum[3] = rk[9] + rk[11] + rk[13] + rk[14] + rk[15];
+            gsum[4] = rk[10] + rk[12];
+            gsum[5] = rk[16] + rk[17] + rk[18];
+            const T q = p.linear ? T(0) : T(1);
+            T sb[Q], kb[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const T s = rate_of<T>(k, p);
+                sb[k] = s * b[k];
+                kb[k] = (T(1) - T(0.5) * s) * b[k];
+            }
+            const T ux = jx + T(0.5) * p.Fx, uy = jy + T(0.5) * p.Fy, uz = jz + T(0.5) * p.Fz;
+            gsum[6] = (double)(b[3] - T(2.0 / 3.0) * b[4] +
+                               q * (T(0.5) * dotP<T>(0, jx, jy, jz, sb) + dotP<T>(0, ux, uy, uz, kb)));
+            gsum[7] = (double)(b[5] - T(2.0 / 3.0) * b[6] +
+                               q * (T(0.5) * dotP<T>(1, jx, jy, jz, sb) + dotP<T>(1, ux, uy, uz, kb)));
+            gsum[8] = (double)(b[7] - T(2.0 / 3.0) * b[8] +
+                               q * (T(0.5) * dotP<T>(2, jx, jy, jz, sb) + dotP<T>(2, ux, uy, uz, kb)));
+            gsum[9] = (double)(d == 0 ? jx : (d == 1 ? jy : jz));
+        }
+    }
+    block_sum_store<10>(gsum, partials);
+}
+
+// Fixed-order sum of NV-component partials by one block.
+template <int NV>
+__global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict__ partials, int nblk,
+                                                        double *out) {
+    __shared__ double sm[NV][1024];
+    double acc[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[a] += partials[(size_t)NV * b + a];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) sm[a][threadIdx.x] = acc[a];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int a = 0; a < NV; ++a) sm[a][threadIdx.x] += sm[a][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < NV) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+SparseMap sparse_map(const lbm_ctx *c);
+
+static AdjView make_adj_view(const lbm_ctx *c) {
+    AdjView v;
+    v.layout = c->opt.layout;
+    v.units = (uint32_t)(c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N);
+    v.lw = c->d_lw;
+    v.sm = sparse_map(c);
+    v.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
+    return v;
+}
+
+template <typename T>
+static Collide<T> collide_params(const lbm_ctx *c) {
+    Collide<T> p;
+    p.se = (T)c->s[1];
+    p.seps = (T)c->s[2];
+    p.sq = (T)c->s[4];
+    p.snu = (T)c->s[9];
+    p.spi = (T)c->s[10];
+    p.sm = (T)c->s[16];
+    p.Fx = (T)c->F[0];
+    p.Fy = (T)c->F[1];
+    p.Fz = (T)c->F[2];
+    p.linear = c->opt.linear_eq;
+    return p;
+}
+
+int launch_step(lbm_ctx *c, bool reduce);
+
+template <typename T>
+static void capture(lbm_ctx *c, const AdjView &v, unsigned grid, T *H, int average) {
+    const AdjState st{c->opt.layout, (int)(c->steps & 1)};
+    const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    const void *A = c->opt.layout == LBM_LAYOUT_AB ? c->d_pop[c->cur] : c->d_pop[0];
+    switch (c->opt.precision) {
+    case LBM_FP64:
+        k_adj_capture<double><<<grid, 256, 0, c->stream>>>((const double *)A, v, st, lds,
+                                                           (double *)H, average);
+        break;
+    case LBM_FP32_SHIFTED:
+        k_adj_capture<float><<<grid, 256, 0, c->stream>>>((const float *)A, v, st, lds, (float *)H,
+                                                          average);
+        break;
+    default:
+        k_adj_capture<__half><<<grid, 256, 0, c->stream>>>((const __half *)A, v, st, lds,
+                                                           (float *)H, average);
+        break;
+    }
+    c->launches++;
+}
+
+// Runs the adjoint iteration and the gradient pass in arithmetic type T.
+// sums[0..9] receive the raw gradient sums (see k_adj_grad); *iters and
+// *resid the iteration count and final relative residual.  The context
+// advances one step (the linearisation point is a two-step mean).
+template <typename T>
+static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double coef,
+                       double sums[10], int64_t *iters, double *resid) {
+    const AdjView v = make_adj_view(c);
+    const size_t bytes = sizeof(T) * Q * (size_t)v.units;
+    T *H = nullptr, *cur = nullptr, *prev = nullptr;
+    double *part = nullptr, *dsum = nullptr;
+    const unsigned grid = (unsigned)((v.units + 255) / 256);
+    cudaError_t e = cudaMalloc(&H, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&cur, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&prev, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 10 * (size_t)(grid > 0 ? grid : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&dsum, sizeof(double) * 10);
+    auto cleanup = [&]() {
+        cudaFree(H);
+        cudaFree(cur);
+        cudaFree(prev);
+        cudaFree(part);
+        cudaFree(dsum);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return launch_error(e);
+    }
+    const Collide<T> p = collide_params<T>(c);
+    *iters = 0;
+    *resid = NAN;
+    for (int a = 0; a < 10; ++a) sums[a] = 0.0;
+    if (grid > 0) {
+        // H = (streamed state now + streamed state after one more step) / 2
+        capture<T>(c, v, grid, H, 0);
+        launch_step(c, false);
+        capture<T>(c, v, grid, H, 1);
+        // psi_{-1} = psi_0 = 0: the first step gives psi_1 = dJ/dh
+        e = cudaMemsetAsync(cur, 0, bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0, bytes, c->stream);
+        const int64_t K = c->opt.check_interval > 0 ? c->opt.check_interval : 100;
+        double host[2];
+        while (e == cudaSuccess && *iters < max_iter) {
+            const bool check = *iters >= 1 && (((*iters + 1) % K == 0) || (*iters + 1 == max_iter));
+            // prev <- J^T S^T cur + g (prev held the iterate before cur)
+            k_adj_step<T><<<grid, 256, 0, c->stream>>>(H, cur, prev, v, p, (T)coef, d,
+                                                       check ? part : nullptr);
+            c->launches++;
+            T *t = cur;
+            cur = prev;
+            prev = t;
+            ++*iters;
+            if (check) {
+                k_sum_partials<2><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum);
+                c->launches++;
+                e = cudaMemcpyAsync(host, dsum, sizeof host, cudaMemcpyDeviceToHost, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess) break;
+                *resid = host[1] > 0.0 ? sqrt(host[0] / host[1]) : 0.0;
+                if (!isfinite(*resid)) {
+                    cleanup();
+                    return LBM_EUNSTABLE;
+                }
+                if (*resid <= tol) break;
+            }
+        }
+        if (e == cudaSuccess) {
+            k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, cur, prev, v, p, d, part);
+            k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum);
+            c->launches += 2;
+            e = cudaMemcpyAsync(sums, dsum, sizeof(double) * 10, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cleanup();
+    return launch_error(e);
+}
+
+int adjoint_sums(lbm_ctx *c, double tol, int64_t max_iter, int d, double coef, double sums[10],
+                 int64_t *iters, double *resid) {
+    if (c->opt.precision == LBM_FP64)
+        return adjoint_run<double>(c, tol, max_iter, d, coef, sums, iters, resid);
+    return adjoint_run<float>(c, tol, max_iter, d, coef, sums, iters, resid);
+}
+
+}  // namespace lbm

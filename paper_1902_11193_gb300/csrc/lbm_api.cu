@@ -21,6 +21,8 @@ void launch_finalize(lbm_ctx *c, int nblk, double inv_total, double *out_dev);
 int build_dense_links(lbm_ctx *c, unsigned long long *d_links);
 int build_sparse_links(lbm_ctx *c, unsigned long long *d_links);
 int export_sparse_nbr(lbm_ctx *c, int32_t *nbr_dev);
+int adjoint_sums(lbm_ctx *c, double tol, int64_t max_iter, int d, double coef, double sums[10],
+                 int64_t *iters, double *resid);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -52,6 +54,7 @@ void lbm_default_options(lbm_options *o) {
     o->cuda_stream = nullptr;
     o->fp16_scale_log2 = 0;
     o->block_size = 0;
+    o->stop_rule = 0;
 }
 
 // Table 2 (Sec. 2.3); s_nu = 1/tau in every set.
@@ -95,6 +98,7 @@ static void free_ctx(lbm_ctx *c) {
     cudaFree(c->d_lw);
     cudaFree(c->d_fidx);
     cudaFree(c->d_bb);
+    cudaFree(c->d_nb);
     cudaFree(c->d_rw);
     cudaFree(c->d_rstart);
     cudaFree(c->d_pop[0]);
@@ -144,6 +148,7 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     if (o.check_interval < 1) o.check_interval = 1;
     if (o.max_steps <= 0) o.max_steps = 1000000;
     if (o.fp16_scale_log2 < 0 || o.fp16_scale_log2 > 60) return LBM_EINVAL;
+    if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
     int64_t Nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         if (mask[n] > 1) return LBM_EINVAL;
@@ -161,6 +166,9 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     c->tau = 1.0 / s[9];
     memcpy(c->F, force, sizeof c->F);
     c->opt = o;
+    c->set = -1;
+    c->Lambda = NAN;
+    c->converged = false;
     c->h_mask = (uint8_t *)malloc((size_t)N);
     if (!c->h_mask) {
         delete c;
@@ -197,6 +205,7 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     if (sparse) {
         CKF(cudaMalloc(&c->d_fidx, sizeof(int32_t) * (size_t)(Nf > 0 ? Nf : 1)));
         CKF(cudaMalloc(&c->d_bb, sizeof(uint32_t) * (size_t)(Nf > 0 ? Nf : 1)));
+        CKF(cudaMalloc(&c->d_nb, sizeof(uint2) * (size_t)(Nf > 0 ? Nf : 1)));
         c->Wr = (c->Lx + 31) / 32;
         const size_t nrows = (size_t)c->Ly * c->Lz;
         CKF(cudaMalloc(&c->d_rw, sizeof(RowWord) * nrows * c->Wr));
@@ -250,7 +259,12 @@ int lbm_create(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], int32_
     double s[19];
     int rc = lbm_rates(set, tau, Lambda, s);
     if (rc != LBM_OK) return rc;
-    return lbm_create_rates(out, mask, dims, s, force, opt);
+    rc = lbm_create_rates(out, mask, dims, s, force, opt);
+    if (rc == LBM_OK) {
+        (*out)->set = set;
+        (*out)->Lambda = Lambda;
+    }
+    return rc;
 }
 
 void lbm_destroy(lbm_ctx *c) {
@@ -261,6 +275,7 @@ void lbm_destroy(lbm_ctx *c) {
 
 int lbm_step(lbm_ctx *c, int64_t n) {
     if (!c || n < 0) return LBM_EINVAL;
+    if (n > 0) c->converged = c->has_conv = false;
     for (int64_t t = 0; t < n; ++t) launch_step(c, false);
     CK(cudaGetLastError());
     return LBM_OK;
@@ -290,13 +305,48 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
     int d = 0;
     for (int a = 1; a < 3; ++a)
         if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
-    const int64_t K = c->opt.check_interval, maxs = c->opt.max_steps;
+    const int rule = c->opt.stop_rule;
+    const int64_t K = rule == 1 && c->opt.check_interval < 3 ? 3 : c->opt.check_interval;
+    const int64_t maxs = c->opt.max_steps;
     int64_t done = 0;
+    c->converged = false;
+    c->has_conv = false;
     double Ua = NAN, Ub = NAN;
+    double Uc3[3] = {NAN, NAN, NAN};
     int rc = LBM_ENOTCONV;
     while (done < maxs) {
         int64_t chunk = K < maxs - done ? K : maxs - done;
         int rr;
+        if (rule == 1) {
+            // the mean of two consecutive steps, from the chunk's last three
+            if (chunk < 3) {
+                for (int64_t t = 0; t < chunk; ++t) launch_step(c, false);
+                CK(cudaGetLastError());
+                done += chunk;
+                break;
+            }
+            for (int64_t t = 0; t < chunk - 3; ++t) launch_step(c, false);
+            measured_step(c, 0);
+            measured_step(c, 1);
+            measured_step(c, 2);
+            CK(cudaGetLastError());
+            rr = read_U(c, 3);
+            if (rr) return rr;
+            for (int a = 0; a < 3; ++a) Uc3[a] = 0.5 * (c->h_U[3 + a] + c->h_U[6 + a]);
+            Ua = 0.5 * (c->h_U[d] + c->h_U[3 + d]);
+            Ub = Uc3[d];
+            done += chunk;
+            const int flag = *(int *)(c->h_U + 24);
+            if (flag || !isfinite(c->h_U[6]) || !isfinite(c->h_U[7]) || !isfinite(c->h_U[8])) {
+                rc = LBM_EUNSTABLE;
+                break;
+            }
+            if (fabs(Ub - Ua) <= tol * fabs(Ub)) {
+                rc = LBM_OK;
+                break;
+            }
+            continue;
+        }
         if (K >= 2 && chunk >= 2) {
             for (int64_t t = 0; t < chunk - 2; ++t) launch_step(c, false);
             measured_step(c, 0);
@@ -320,13 +370,99 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
             rc = LBM_EUNSTABLE;
             break;
         }
+        for (int a = 0; a < 3; ++a) Uc3[a] = c->h_U[3 + a];
         if (isfinite(Ua) && fabs(Ub - Ua) <= tol * fabs(Ub)) {
             rc = LBM_OK;
             break;
         }
     }
     if (steps_taken) *steps_taken = done;
+    c->converged = rc == LBM_OK;
+    if (rc == LBM_OK || rc == LBM_ENOTCONV) {
+        c->has_conv = isfinite(Uc3[0]);
+        for (int a = 0; a < 3; ++a) c->U_conv[a] = Uc3[a];
+    }
     return rc;
+}
+
+int lbm_converged_velocity(lbm_ctx *c, double U[3]) {
+    if (!c || !U) return LBM_EINVAL;
+    if (!c->has_conv) return LBM_ENOSTATE;
+    for (int a = 0; a < 3; ++a) U[a] = c->U_conv[a];
+    return LBM_OK;
+}
+
+int lbm_converged_permeability(lbm_ctx *c, double k[3]) {
+    if (!c || !k) return LBM_EINVAL;
+    if (!c->has_conv) return LBM_ENOSTATE;
+    const double nu = (c->tau - 0.5) / 3.0;
+    for (int a = 0; a < 3; ++a) k[a] = c->F[a] != 0.0 ? nu * c->U_conv[a] / c->F[a] : NAN;
+    return LBM_OK;
+}
+
+// d s_E / d s_nu and d s_E / d Lambda for s_E = 2(2 - s)/(4 Lambda s - s + 2)
+// (eq. Magic param solved for the odd rate).
+static double dsE_ds(double s, double L) {
+    const double den = 4.0 * L * s - s + 2.0;
+    return -16.0 * L / (den * den);
+}
+static double dsE_dL(double s, double L) {
+    const double den = 4.0 * L * s - s + 2.0;
+    return -8.0 * s * (2.0 - s) / (den * den);
+}
+
+int lbm_adjoint(lbm_ctx *c, double tol, int64_t max_iter, lbm_grad *out) {
+    if (!c || !out || !(tol >= 0.0) || max_iter < 1) return LBM_EINVAL;
+    if (!c->converged) return LBM_ENOSTATE;
+    int d = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
+    if (c->F[d] == 0.0) return LBM_EINVAL;
+    const double tau = c->tau, sn = c->s[9], nu = (tau - 0.5) / 3.0, Fd = c->F[d];
+    const double Nd = (double)c->N;
+    double sums[10];
+    int64_t iters = 0;
+    double resid = NAN;
+    int rc = adjoint_sums(c, tol, max_iter, d, nu / (Fd * Nd), sums, &iters, &resid);
+    if (rc) return rc;
+    double U[3] = {0.0, 0.0, 0.0};
+    U[d] = sums[9] / Nd;  // mean velocity of the linearisation point (a two-step mean)
+    // rate groups (e, eps, q, nu, pi, m): d s_g / d s_nu under the set's rules
+    double g[6] = {0, 0, 0, 1, 0, 0};
+    const double dk8 = dsE_ds(sn, 3.0 / 16.0), dk4 = dsE_ds(sn, 3.0 / 8.0);
+    double Lq = NAN, Lm = NAN;
+    switch (c->set) {
+    case LBM_SET_A: g[0] = g[1] = g[2] = g[4] = g[5] = dk8; break;
+    case LBM_SET_B: g[0] = g[1] = g[4] = 1; g[2] = g[5] = dk8; Lq = Lm = 3.0 / 16.0; break;
+    case LBM_SET_C: break;
+    case LBM_SET_D: g[0] = g[1] = g[4] = 1; g[2] = dk8; g[5] = dk4; Lq = 3.0 / 16.0; Lm = 3.0 / 8.0; break;
+    case LBM_SET_E:
+        g[0] = g[1] = g[4] = 1;
+        g[2] = g[5] = dsE_ds(sn, c->Lambda);
+        Lq = Lm = c->Lambda;
+        break;
+    case LBM_SET_SRT: g[0] = g[1] = g[2] = g[4] = g[5] = 1; break;
+    default: break;  // rates given directly: tau acts through s_nu only
+    }
+    const double dsn_dtau = -1.0 / (tau * tau);
+    double dtau = U[d] / (3.0 * Fd);  // explicit: J = nu(tau) U / F
+    for (int q = 0; q < 6; ++q) dtau += sums[q] * g[q] * dsn_dtau;
+    out->dk_dtau = dtau;
+    if (isfinite(Lq)) {
+        out->dk_dLambda_q = sums[2] * dsE_dL(sn, Lq);
+        out->dk_dLambda_m = sums[5] * dsE_dL(sn, Lm);
+        out->dk_dLambda = out->dk_dLambda_q + out->dk_dLambda_m;
+    } else {
+        out->dk_dLambda = out->dk_dLambda_q = out->dk_dLambda_m = NAN;
+    }
+    for (int a = 0; a < 3; ++a) out->dk_dF[a] = sums[6 + a];
+    // explicit: U_d carries F_d/2 at every fluid node, and J divides by F_d
+    out->dk_dF[d] += nu * ((double)c->Nf / (2.0 * Nd)) / Fd - nu * U[d] / (Fd * Fd);
+    for (int q = 0; q < 6; ++q) out->dk_ds[q] = sums[q];
+    out->k = nu * U[d] / Fd;
+    out->iterations = iters;
+    out->residual = resid;
+    return LBM_OK;
 }
 
 int lbm_mean_velocity(lbm_ctx *c, double U[3]) {
@@ -388,6 +524,7 @@ int lbm_get_populations(lbm_ctx *c, double *f) {
 
 int lbm_set_populations(lbm_ctx *c, const double *f) {
     if (!c || !f) return LBM_EINVAL;
+    c->converged = c->has_conv = false;
     double *d_f = nullptr;
     const size_t bytes = sizeof(double) * 19 * (size_t)c->N;
     CK(cudaMalloc(&d_f, bytes));
@@ -471,7 +608,7 @@ struct CkptHeader {
     int64_t max_steps;
     int64_t steps;
     int32_t cur;
-    int32_t pad;
+    int32_t stop_rule;
 };
 
 int lbm_save(lbm_ctx *c, const char *path) {
@@ -502,6 +639,7 @@ int lbm_save(lbm_ctx *c, const char *path) {
     h.max_steps = c->opt.max_steps;
     h.steps = c->steps;
     h.cur = 0;
+    h.stop_rule = c->opt.stop_rule;
     FILE *fp = fopen(path, "wb");
     if (!fp) return LBM_EIO;
     bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(c->h_mask, 1, (size_t)c->N, fp) == (size_t)c->N &&
@@ -540,6 +678,7 @@ int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
     o.fp16_scale_log2 = h.fp16_scale_log2;
     o.block_size = h.block_size;
     o.max_steps = h.max_steps;
+    o.stop_rule = h.stop_rule;
     lbm_ctx *c = nullptr;
     int rc = lbm_create_rates(&c, mask.data(), h.dims, h.s, h.F, &o);
     if (rc != LBM_OK) {

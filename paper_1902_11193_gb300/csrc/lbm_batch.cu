@@ -1,0 +1,688 @@
+// Batched parameter sweep: many lattices stepped by one persistent kernel.
+//
+// The paper's study (Secs. 4.1-4.3) runs the same solver over Sets A-E, a
+// tau sweep and several geometries and resolutions.  Small lattices are
+// launch-bound when stepped one by one, so the batch flattens every active
+// lattice into a table of 256*npt-unit tiles and a persistent cooperative
+// kernel walks the table once per time step, with a grid barrier between
+// steps (each lattice's AA step t+1 reads what step t wrote).  The barrier
+// waits are bounded in time: on expiry the kernel raises an error flag and
+// returns, and the host reports LBM_ETIMEOUT.  In the last two steps of a
+// chunk each tile adds its lattice's shifted velocity to FP64 partials, a
+// per-lattice kernel sums them in a fixed order, and the host applies each
+// lattice's stopping rule and retires converged lattices from the table.
+// The chunk (step-count upload, persistent kernel, reductions, result copy)
+// is captured once in a CUDA graph and replayed; the tile table lives in
+// device memory, so retiring lattices does not change the graph.
+// Every lattice is an ordinary lbm_ctx (its own populations and link
+// tables), so all single-lattice readers work on batch members, and the
+// per-unit update is the same code as the single-lattice kernels
+// (lbm_step.cuh): a batch member's state is bitwise the state of the same
+// lattice run alone with the same check interval.
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+SparseMap sparse_map(const lbm_ctx *c);
+
+struct BatchLat {
+    int layout;  // LBM_LAYOUT_AA or LBM_LAYOUT_SPARSE
+    int npt;     // units per thread per tile
+    uint32_t units;
+    void *pop;
+    const uint32_t *lw;
+    SparseMap sm;
+    Dims d;
+    double s6[6];  // se, seps, sq, snu, spi, sm
+    double F[3];
+    int linear;
+    double inv_N;
+};
+
+struct Tile {
+    int lat;
+    uint32_t first;
+};
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int skip;  // block that skips its first arrival (test hook), -1 for none
+};
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a bounded wait: returns false (and raises bar->err)
+// when the other blocks did not all arrive within timeout_ns.
+__device__ bool grid_sync(GridBar *bar, unsigned nblocks, uint64_t timeout_ns, bool skip) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &bar->gen;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (!skip && atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        }
+        const uint64_t t0 = now_ns();
+        while (*vgen == g0) {
+            if (*(volatile int *)&bar->err || now_ns() - t0 > timeout_ns) {
+                atomicExch(&bar->err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(200);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_batch(const BatchLat *__restrict__ lats,
+                                               const Tile *__restrict__ tiles,
+                                               const int *__restrict__ ntiles_p,
+                                               const int64_t *__restrict__ lat_steps, int nsteps,
+                                               int nmeas,
+                                               double *__restrict__ tile_part, int max_tiles,
+                                               GridBar *bar, uint64_t timeout_ns) {
+    using C = typename Store<S>::C;
+    const int ntiles = *ntiles_p;
+    __shared__ int skip_me;
+    if (threadIdx.x == 0) skip_me = (*(volatile int *)&bar->skip == (int)blockIdx.x);
+    __syncthreads();
+    for (int s = 0; s < nsteps; ++s) {
+        const int slot = s - (nsteps - nmeas);  // >= 0: one of the last nmeas steps
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const Tile tl = tiles[t];
+            const BatchLat &L = lats[tl.lat];
+            Collide<C> p;
+            p.se = (C)L.s6[0];
+            p.seps = (C)L.s6[1];
+            p.sq = (C)L.s6[2];
+            p.snu = (C)L.s6[3];
+            p.spi = (C)L.s6[4];
+            p.sm = (C)L.s6[5];
+            p.Fx = (C)L.F[0];
+            p.Fy = (C)L.F[1];
+            p.Fz = (C)L.F[2];
+            p.linear = L.linear;
+            const bool odd = ((lat_steps[tl.lat] + s) & 1) != 0;
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < L.npt; ++r) {
+                const uint32_t u = tl.first + (uint32_t)r * blockDim.x + threadIdx.x;
+                if (u >= L.units) break;
+                C jx = C(0), jy = C(0), jz = C(0);
+                bool fl = true;
+                S *A = (S *)L.pop;
+                if (L.layout == LBM_LAYOUT_SPARSE) {
+                    if (odd)
+                        aa_sparse_update<S, true, size_t>(A, L.sm, L.units, u, __ldg(L.sm.nb + u), p,
+                                                          1.f, 1.f, jx, jy, jz);
+                    else
+                        aa_sparse_update<S, false, size_t>(A, L.sm, L.units, u, make_uint2(0u, 0u),
+                                                           p, 1.f, 1.f, jx, jy, jz);
+                } else {
+                    const uint32_t w = L.lw[u];
+                    fl = odd ? aa_dense_update<S, true>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz)
+                             : aa_dense_update<S, false>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz);
+                }
+                if (slot >= 0 && fl) {
+                    acc[0] += (double)jx;
+                    acc[1] += (double)jy;
+                    acc[2] += (double)jz;
+                }
+            }
+            if (slot >= 0) {
+                __shared__ double sm[32][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o);
+                if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) sm[threadIdx.x >> 5][a] = acc[a];
+                __syncthreads();
+                if (threadIdx.x < 3) {
+                    double v = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sm[w][threadIdx.x];
+                    tile_part[((size_t)slot * max_tiles + t) * 3 + threadIdx.x] = v;
+                }
+                __syncthreads();
+            }
+        }
+        if (s + 1 < nsteps && !grid_sync(bar, gridDim.x, timeout_ns, s == 0 && skip_me)) return;
+    }
+}
+
+// U[i][slot][a] = (sum over lattice i's tiles, in tile order) / N_i, for the
+// three measurement slots.
+__global__ void __launch_bounds__(256) k_batch_finalize(const BatchLat *__restrict__ lats,
+                                                        const int2 *__restrict__ lat_tiles,
+                                                        const double *__restrict__ tile_part,
+                                                        int max_tiles, double *U) {
+    const int i = blockIdx.x;
+    const int2 rng = lat_tiles[i];
+    __shared__ double sm[9][256];
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < rng.y; t += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            acc[q] += tile_part[((size_t)(q / 3) * max_tiles + rng.x + t) * 3 + (q % 3)];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sm[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 9) U[(size_t)9 * i + threadIdx.x] = sm[threadIdx.x][0] * lats[i].inv_N;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+    int n;
+    std::vector<lbm_ctx *> ctx;
+    lbm_batch_options opt;
+    cudaStream_t stream;
+    bool own_stream;
+    std::vector<int> layout, npt;
+    std::vector<char> active;
+    std::vector<int64_t> steps;
+    std::vector<int> status;
+    std::vector<double> Ua, Ub;
+    BatchLat *d_lats;
+    Tile *d_tiles;
+    int *d_ntiles;
+    int2 *d_lat_tiles;
+    int64_t *d_steps, *h_steps;
+    double *d_tile_part;
+    int max_tiles;
+    GridBar *d_bar;
+    double *d_U, *h_U;
+    int *h_err;
+    int grid;
+    cudaGraphExec_t gexec;
+    bool graph_ok;
+    bool failed;
+    int64_t launches;
+    uint64_t timeout_ns;
+};
+
+extern "C" {
+
+void lbm_batch_default_options(lbm_batch_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = LBM_FP32_SHIFTED;
+    o->layout = -1;
+    o->nodes_per_thread = 0;
+    o->check_interval = 100;
+    o->max_steps = 1000000;
+    o->use_graph = 1;
+    o->barrier_timeout_ms = 2000;
+    o->test_skip_block = -1;
+    o->stop_rule = 0;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (lbm_ctx *c : b->ctx) lbm_destroy(c);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    cudaFree(b->d_lats);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_ntiles);
+    cudaFree(b->d_lat_tiles);
+    cudaFree(b->d_steps);
+    cudaFree(b->d_tile_part);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_U);
+    cudaFreeHost(b->h_steps);
+    cudaFreeHost(b->h_U);
+    cudaFreeHost(b->h_err);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"
+
+namespace {
+
+BatchLat make_lat(const lbm_ctx *c, int npt) {
+    BatchLat L;
+    memset(&L, 0, sizeof L);
+    L.layout = c->opt.layout;
+    L.npt = npt;
+    L.units = (uint32_t)(c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N);
+    L.pop = c->d_pop[0];
+    L.lw = c->d_lw;
+    if (c->opt.layout == LBM_LAYOUT_SPARSE) L.sm = sparse_map(c);
+    L.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
+    const int ks[6] = {1, 2, 4, 9, 10, 16};
+    for (int q = 0; q < 6; ++q) L.s6[q] = c->s[ks[q]];
+    for (int a = 0; a < 3; ++a) L.F[a] = c->F[a];
+    L.linear = c->opt.linear_eq;
+    L.inv_N = 1.0 / (double)c->N;
+    return L;
+}
+
+int ntiles_of(const BatchLat &L) { return (int)((L.units + 256u * L.npt - 1) / (256u * L.npt)); }
+
+int coop_grid(int precision) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (precision == LBM_FP64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<double>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 256, 0);
+    return sms * (per > 0 ? per : 1);
+}
+
+// Uploads the tile table of the active lattices.
+cudaError_t upload_tiles(lbm_batch *b, const std::vector<BatchLat> &lats) {
+    std::vector<Tile> tiles;
+    std::vector<int2> ranges(b->n, make_int2(0, 0));
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->active[i]) continue;
+        const int nt = ntiles_of(lats[i]);
+        ranges[i] = make_int2((int)tiles.size(), nt);
+        for (int t = 0; t < nt; ++t) tiles.push_back(Tile{i, (uint32_t)t * 256u * lats[i].npt});
+    }
+    const int nt = (int)tiles.size();
+    cudaError_t e = cudaSuccess;
+    if (nt) e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_lat_tiles, ranges.data(), sizeof(int2) * b->n, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors go out of scope
+    return e;
+}
+
+cudaError_t enqueue_chunk(lbm_batch *b) {
+    cudaError_t e = cudaMemcpyAsync(b->d_steps, b->h_steps, sizeof(int64_t) * b->n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return e;
+    int K = b->opt.check_interval;
+    int nmeas = b->opt.stop_rule == 1 ? 3 : 2;
+    void *args[] = {&b->d_lats, &b->d_tiles, &b->d_ntiles, &b->d_steps, &K, &nmeas,
+                    &b->d_tile_part, &b->max_tiles, &b->d_bar, &b->timeout_ns};
+    const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
+                                                  : (const void *)k_batch<float>;
+    e = cudaLaunchCooperativeKernel(fn, dim3(b->grid), dim3(256), args, 0, b->stream);
+    if (e != cudaSuccess) return e;
+    k_batch_finalize<<<b->n, 256, 0, b->stream>>>(b->d_lats, b->d_lat_tiles, b->d_tile_part,
+                                                  b->max_tiles, b->d_U);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(b->h_U, b->d_U, sizeof(double) * 9 * b->n, cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(b->h_err, &b->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+}
+
+// Autotuner: device time of `steps` batch steps of one lattice in a given
+// layout and nodes-per-thread, measured with events on the batch stream.
+float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
+    BatchLat L = make_lat(c, npt);
+    const int nt = ntiles_of(L);
+    std::vector<Tile> tiles;
+    for (int t = 0; t < nt; ++t) tiles.push_back(Tile{0, (uint32_t)t * 256u * npt});
+    BatchLat *d_l = nullptr;
+    Tile *d_t = nullptr;
+    int *d_n = nullptr;
+    int64_t *d_s = nullptr;
+    double *d_p = nullptr;
+    GridBar *d_b = nullptr;
+    float ms = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&d_l, sizeof L) == cudaSuccess && cudaMalloc(&d_t, sizeof(Tile) * nt) == cudaSuccess &&
+        cudaMalloc(&d_n, sizeof(int)) == cudaSuccess && cudaMalloc(&d_s, sizeof(int64_t)) == cudaSuccess &&
+        cudaMalloc(&d_p, sizeof(double) * 9 * nt) == cudaSuccess &&
+        cudaMalloc(&d_b, sizeof(GridBar)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess) {
+        const int64_t zero = 0;
+        GridBar gb{0u, 0u, 0, -1};
+        cudaMemcpyAsync(d_l, &L, sizeof L, cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(d_t, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(d_n, &nt, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(d_s, &zero, sizeof zero, cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(d_b, &gb, sizeof gb, cudaMemcpyHostToDevice, b->stream);
+        int grid = b->grid < nt ? b->grid : nt;
+        int maxt = nt;
+        int nmeas = 2;
+        void *args[] = {&d_l, &d_t, &d_n, &d_s, &steps, &nmeas, &d_p, &maxt, &d_b, &b->timeout_ns};
+        const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
+                                                      : (const void *)k_batch<float>;
+        cudaEventRecord(e0, b->stream);
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, b->stream);
+        cudaEventRecord(e1, b->stream);
+        int err = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &d_b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess && !err) cudaEventElapsedTime(&ms, e0, e1);
+        b->launches++;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_l);
+    cudaFree(d_t);
+    cudaFree(d_n);
+    cudaFree(d_s);
+    cudaFree(d_p);
+    cudaFree(d_b);
+    return ms;
+}
+
+std::string mask_key(const lbm_lattice_desc &d) {
+    const size_t N = (size_t)d.dims[0] * d.dims[1] * d.dims[2];
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the mask bytes
+    for (size_t i = 0; i < N; ++i) h = (h ^ d.mask[i]) * 1099511628211ull;
+    char buf[96];
+    snprintf(buf, sizeof buf, "%d.%d.%d.%016llx", d.dims[0], d.dims[1], d.dims[2],
+             (unsigned long long)h);
+    return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
+                     const lbm_batch_options *opt) {
+    if (!out || n <= 0 || !desc) return LBM_EINVAL;
+    *out = nullptr;
+    lbm_batch_options o;
+    lbm_batch_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != LBM_FP32_SHIFTED && o.precision != LBM_FP64) return LBM_EINVAL;
+    if (o.layout != -1 && o.layout != LBM_LAYOUT_AA && o.layout != LBM_LAYOUT_SPARSE) return LBM_EINVAL;
+    if (o.nodes_per_thread < 0 || o.nodes_per_thread > 2) return LBM_EINVAL;
+    if (o.check_interval < 2) o.check_interval = 2;
+    if (o.max_steps <= 0) o.max_steps = 1000000;
+    if (o.barrier_timeout_ms <= 0) o.barrier_timeout_ms = 2000;
+    if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
+    if (o.stop_rule == 1 && o.check_interval < 3) o.check_interval = 3;
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ENOMEM;
+    b->n = n;
+    b->opt = o;
+    b->timeout_ns = (uint64_t)o.barrier_timeout_ms * 1000000ull;
+    auto fail = [&](int rc) {
+        lbm_batch_destroy(b);
+        return rc;
+    };
+    cudaError_t e;
+    if (o.cuda_stream) {
+        b->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(launch_error(e));
+        b->own_stream = true;
+    }
+    b->grid = coop_grid(o.precision);
+    lbm_options lo;
+    lbm_default_options(&lo);
+    lo.precision = o.precision;
+    lo.check_interval = o.check_interval;
+    lo.linear_eq = o.linear_eq;
+    lo.max_steps = o.max_steps;
+    lo.cuda_stream = b->stream;
+    // autotune per distinct image: layout and nodes per thread
+    std::map<std::string, std::pair<int, int>> tuned;
+    b->layout.resize(n);
+    b->npt.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const lbm_lattice_desc &d = desc[i];
+        if (!d.mask) return fail(LBM_EINVAL);
+        int lay = o.layout, np = o.nodes_per_thread;
+        if (lay == -1 || np == 0) {
+            const std::string key = mask_key(d);
+            auto it = tuned.find(key);
+            if (it == tuned.end()) {
+                float best = INFINITY;
+                int bl = LBM_LAYOUT_AA, bn = 1;
+                for (int cl : {LBM_LAYOUT_AA, LBM_LAYOUT_SPARSE}) {
+                    if (lay != -1 && cl != lay) continue;
+                    lbm_options to = lo;
+                    to.layout = cl;
+                    lbm_ctx *c = nullptr;
+                    int rc = d.set >= 0 ? lbm_create(&c, d.mask, d.dims, d.set, d.tau, d.Lambda, d.force, &to)
+                                        : lbm_create_rates(&c, d.mask, d.dims, d.s, d.force, &to);
+                    if (rc != LBM_OK) return fail(rc);
+                    for (int cn : {1, 2}) {
+                        if (np != 0 && cn != np) continue;
+                        time_candidate(b, c, cn, 2);  // warm-up
+                        const float ms = time_candidate(b, c, cn, 8);
+                        if (ms < best) {
+                            best = ms;
+                            bl = cl;
+                            bn = cn;
+                        }
+                    }
+                    lbm_destroy(c);
+                }
+                it = tuned.emplace(key, std::make_pair(bl, bn)).first;
+            }
+            if (lay == -1) lay = it->second.first;
+            if (np == 0) np = it->second.second;
+        }
+        b->layout[i] = lay;
+        b->npt[i] = np;
+        lbm_options to = lo;
+        to.layout = lay;
+        lbm_ctx *c = nullptr;
+        int rc = d.set >= 0 ? lbm_create(&c, d.mask, d.dims, d.set, d.tau, d.Lambda, d.force, &to)
+                            : lbm_create_rates(&c, d.mask, d.dims, d.s, d.force, &to);
+        if (rc != LBM_OK) return fail(rc);
+        b->ctx.push_back(c);
+    }
+    std::vector<BatchLat> lats(n);
+    int total_tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        lats[i] = make_lat(b->ctx[i], b->npt[i]);
+        total_tiles += ntiles_of(lats[i]);
+    }
+    b->max_tiles = total_tiles > 0 ? total_tiles : 1;
+#define CKB(call)                                        \
+    do {                                                 \
+        cudaError_t e3 = (call);                         \
+        if (e3 != cudaSuccess) return fail(launch_error(e3)); \
+    } while (0)
+    CKB(cudaMalloc(&b->d_lats, sizeof(BatchLat) * n));
+    CKB(cudaMalloc(&b->d_tiles, sizeof(Tile) * b->max_tiles));
+    CKB(cudaMalloc(&b->d_ntiles, sizeof(int)));
+    CKB(cudaMalloc(&b->d_lat_tiles, sizeof(int2) * n));
+    CKB(cudaMalloc(&b->d_steps, sizeof(int64_t) * n));
+    CKB(cudaMalloc(&b->d_tile_part, sizeof(double) * 9 * (size_t)b->max_tiles));
+    CKB(cudaMalloc(&b->d_bar, sizeof(GridBar)));
+    CKB(cudaMalloc(&b->d_U, sizeof(double) * 9 * n));
+    CKB(cudaMallocHost(&b->h_steps, sizeof(int64_t) * n));
+    CKB(cudaMallocHost(&b->h_U, sizeof(double) * 9 * n));
+    CKB(cudaMallocHost(&b->h_err, sizeof(int)));
+    CKB(cudaMemcpyAsync(b->d_lats, lats.data(), sizeof(BatchLat) * n, cudaMemcpyHostToDevice, b->stream));
+    GridBar gb{0u, 0u, 0, o.test_skip_block};
+    CKB(cudaMemcpyAsync(b->d_bar, &gb, sizeof gb, cudaMemcpyHostToDevice, b->stream));
+    CKB(cudaStreamSynchronize(b->stream));
+#undef CKB
+    b->active.assign(n, 1);
+    b->steps.assign(n, 0);
+    b->status.assign(n, LBM_ENOTCONV);
+    b->Ua.assign(n, NAN);
+    b->Ub.assign(n, NAN);
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
+    if (!b || !(tol >= 0.0)) return LBM_EINVAL;
+    if (b->failed) return LBM_ETIMEOUT;
+    std::vector<BatchLat> lats(b->n);
+    for (int i = 0; i < b->n; ++i) lats[i] = make_lat(b->ctx[i], b->npt[i]);
+    // every lattice starts a fresh stopping-rule run
+    for (int i = 0; i < b->n; ++i) {
+        b->active[i] = 1;
+        b->status[i] = LBM_ENOTCONV;
+        b->steps[i] = 0;
+        b->ctx[i]->converged = b->ctx[i]->has_conv = false;
+    }
+    std::vector<int> drive(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const double *F = b->ctx[i]->F;
+        int d = 0;
+        for (int a = 1; a < 3; ++a)
+            if (fabs(F[a]) > fabs(F[d])) d = a;
+        drive[i] = d;
+    }
+    const int64_t K = b->opt.check_interval;
+    bool dirty = true;
+    int nact = b->n;
+    while (nact > 0) {
+        cudaError_t e;
+        if (dirty) {
+            e = upload_tiles(b, lats);
+            if (e != cudaSuccess) return launch_error(e);
+            dirty = false;
+        }
+        for (int i = 0; i < b->n; ++i) b->h_steps[i] = b->ctx[i]->steps;
+        if (b->opt.use_graph && !b->gexec && !b->graph_ok) {
+            // capture the chunk once; fall back to direct launches if the
+            // cooperative launch cannot be captured
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t ec = enqueue_chunk(b);
+                e = cudaStreamEndCapture(b->stream, &g);
+                if (ec == cudaSuccess && e == cudaSuccess &&
+                    cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess)
+                    b->graph_ok = true;
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();  // clear a failed capture
+            if (!b->graph_ok) b->opt.use_graph = 0;
+        }
+        if (b->graph_ok)
+            e = cudaGraphLaunch(b->gexec, b->stream);
+        else
+            e = enqueue_chunk(b);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return launch_error(e);
+        b->launches += 2;
+        if (*b->h_err) {
+            b->failed = true;
+            return LBM_ETIMEOUT;
+        }
+        for (int i = 0; i < b->n; ++i) {
+            if (!b->active[i]) continue;
+            lbm_ctx *c = b->ctx[i];
+            c->steps += K;
+            b->steps[i] += K;
+            // slots 0, 1 (and 2 under stop rule 1) of this chunk's last steps
+            const double *u = b->h_U + 9 * i;
+            double m[3];
+            const double *last;
+            double ua, ub;
+            if (b->opt.stop_rule == 1) {
+                for (int a = 0; a < 3; ++a) m[a] = 0.5 * (u[3 + a] + u[6 + a]);
+                ua = 0.5 * (u[drive[i]] + u[3 + drive[i]]);
+                ub = m[drive[i]];
+                last = u + 6;
+            } else {
+                for (int a = 0; a < 3; ++a) m[a] = u[3 + a];
+                ua = u[drive[i]];
+                ub = u[3 + drive[i]];
+                last = u + 3;
+            }
+            b->Ua[i] = ua;
+            b->Ub[i] = ub;
+            c->has_conv = true;
+            for (int a = 0; a < 3; ++a) c->U_conv[a] = m[a];
+            int st = LBM_ENOTCONV;
+            bool retire = false;
+            if (!isfinite(last[0]) || !isfinite(last[1]) || !isfinite(last[2])) {
+                st = LBM_EUNSTABLE;
+                retire = true;
+            } else if (isfinite(ua) && fabs(ub - ua) <= tol * fabs(ub)) {
+                st = LBM_OK;
+                retire = true;
+            } else if (b->steps[i] >= b->opt.max_steps) {
+                retire = true;
+            }
+            if (retire) {
+                b->status[i] = st;
+                b->active[i] = 0;
+                c->converged = st == LBM_OK;
+                c->has_conv = st != LBM_EUNSTABLE;
+                --nact;
+                dirty = true;
+            }
+        }
+    }
+    for (int i = 0; i < b->n; ++i) {
+        if (steps) steps[i] = b->steps[i];
+        if (status) status[i] = b->status[i];
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_permeability(lbm_batch *b, double *k) {
+    if (!b || !k) return LBM_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        int rc = b->ctx[i]->has_conv ? lbm_converged_permeability(b->ctx[i], k + 3 * i)
+                                     : lbm_permeability(b->ctx[i], k + 3 * i);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_mean_velocity(lbm_batch *b, double *U) {
+    if (!b || !U) return LBM_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        int rc = lbm_mean_velocity(b->ctx[i], U + 3 * i);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *npt) {
+    if (!b) return LBM_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        if (layout) layout[i] = b->layout[i];
+        if (npt) npt[i] = b->npt[i];
+    }
+    return LBM_OK;
+}
+
+lbm_ctx *lbm_batch_lattice(lbm_batch *b, int32_t i) {
+    if (!b || i < 0 || i >= b->n) return nullptr;
+    return b->ctx[i];
+}
+
+int64_t lbm_batch_kernel_launches(const lbm_batch *b) { return b ? b->launches : -1; }
+
+}  // extern "C"

@@ -1,5 +1,5 @@
 // The D3Q19 MRT collision with Guo forcing for one node, on shifted
-// populations g_i = f_i - w_i (rho0 = 1).
+// populations g_i = f_i - w_i (rho0 = 1), and the transforms it is built of.
 //
 // Method (Sec. 2.2.1): m = M f; rho = m0; j = (m3, m5, m7) + F/2 (shifted
 // velocity); m* = m - S (m - m^eq) + (I - S/2) m^F (eq. MRT-LBE with the
@@ -13,17 +13,35 @@
 // m^F = M F_i of eq. (Guo_Forcing) are applied in closed form.
 // Shifting only removes M w = (1, -11, 3, 0, ...), i.e. the rho-proportional
 // parts of m0, m1, m2, so rho enters as the deviation m0(g).
+//
+// Moment index: 0 rho, 1 e, 2 eps, 3 jx, 4 qx, 5 jy, 6 qy, 7 jz, 8 qz,
+// 9 3pxx, 10 3pixx, 11 pww, 12 piww, 13 pxy, 14 pyz, 15 pxz, 16 mx, 17 my,
+// 18 mz.
 #pragma once
 
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
+// Squared row norms D_k of M.
 template <typename T>
-__device__ __forceinline__ void mrt_collide(T g[Q], const Collide<T> &p, T &jx_out, T &jy_out,
-                                            T &jz_out) {
-    const T half = T(0.5);
-    // opposite-pair sums (even part) and differences (odd part)
+__device__ __forceinline__ T inv_norm(int k) {
+    return k == 0 ? T(1.0 / 19.0)
+         : k == 1 ? T(1.0 / 2394.0)
+         : k == 2 ? T(1.0 / 252.0)
+         : (k == 3 || k == 5 || k == 7) ? T(0.1)
+         : (k == 4 || k == 6 || k == 8) ? T(0.025)
+         : k == 9 ? T(1.0 / 36.0)
+         : k == 10 ? T(1.0 / 72.0)
+         : k == 11 ? T(1.0 / 12.0)
+         : k == 12 ? T(1.0 / 24.0)
+         : k <= 15 ? T(0.25)
+                   : T(0.125);
+}
+
+// m = M g.
+template <typename T>
+__device__ __forceinline__ void moments_of(const T g[Q], T m[Q]) {
     const T sx = g[1] + g[2], dx = g[1] - g[2];
     const T sy = g[3] + g[4], dy = g[3] - g[4];
     const T sz = g[5] + g[6], dz = g[5] - g[6];
@@ -33,127 +51,153 @@ __device__ __forceinline__ void mrt_collide(T g[Q], const Collide<T> &p, T &jx_o
     const T s4 = g[13] + g[14], d4 = g[13] - g[14];    // (1, 0,-1)
     const T s5 = g[15] + g[16], d5 = g[15] - g[16];    // (0, 1, 1)
     const T s6 = g[17] + g[18], d6 = g[17] - g[18];    // (0, 1,-1)
-
     const T sa = sx + sy + sz;
     const T sxy = s1 + s2, sxz = s3 + s4, syz = s5 + s6;
     const T se = sxy + sxz + syz;
-
-    // moments of the shifted populations
-    const T rho = g[0] + sa + se;                         // m0 (deviation from rho0)
-    const T e = T(-30) * g[0] - T(11) * sa + T(8) * se;   // m1
-    const T eps = T(12) * g[0] - T(4) * sa + se;          // m2
-    const T ex = d1 + d2 + d3 + d4;                       // edge part of x-odd moments
+    m[0] = g[0] + sa + se;
+    m[1] = T(-30) * g[0] - T(11) * sa + T(8) * se;
+    m[2] = T(12) * g[0] - T(4) * sa + se;
+    const T ex = d1 + d2 + d3 + d4;  // edge part of the x-odd moments
     const T ey = d1 - d2 + d5 + d6;
     const T ez = d3 - d4 + d5 - d6;
-    const T jxr = dx + ex, qx = T(-4) * dx + ex;          // m3, m4
-    const T jyr = dy + ey, qy = T(-4) * dy + ey;           // m5, m6
-    const T jzr = dz + ez, qz = T(-4) * dz + ez;           // m7, m8
-    const T pxx = T(2) * sx - sy - sz + sxy + sxz - T(2) * syz;       // m9
-    const T pixx = T(-4) * sx + T(2) * (sy + sz) + sxy + sxz - T(2) * syz;  // m10
-    const T pww = sy - sz + sxy - sxz;                      // m11
-    const T piww = T(2) * (sz - sy) + sxy - sxz;            // m12
-    const T pxy = s1 - s2;                                  // m13
-    const T pyz = s5 - s6;                                  // m14
-    const T pxz = s3 - s4;                                  // m15
-    const T mx = d1 + d2 - d3 - d4;                         // m16
-    const T my = d5 + d6 - d1 + d2;                         // m17
-    const T mz = d3 - d4 - d5 + d6;                         // m18
+    m[3] = dx + ex;
+    m[4] = T(-4) * dx + ex;
+    m[5] = dy + ey;
+    m[6] = T(-4) * dy + ey;
+    m[7] = dz + ez;
+    m[8] = T(-4) * dz + ez;
+    m[9] = T(2) * sx - sy - sz + sxy + sxz - T(2) * syz;
+    m[10] = T(-4) * sx + T(2) * (sy + sz) + sxy + sxz - T(2) * syz;
+    m[11] = sy - sz + sxy - sxz;
+    m[12] = T(2) * (sz - sy) + sxy - sxz;
+    m[13] = s1 - s2;
+    m[14] = s5 - s6;
+    m[15] = s3 - s4;
+    m[16] = d1 + d2 - d3 - d4;
+    m[17] = d5 + d6 - d1 + d2;
+    m[18] = d3 - d4 - d5 + d6;
+}
 
-    // shifted momentum j = sum c f + F/2 = rho0 u
-    const T jx = jxr + half * p.Fx, jy = jyr + half * p.Fy, jz = jzr + half * p.Fz;
+// g = M^T a (so g = M^-1 m for a_k = m_k / D_k).
+template <typename T>
+__device__ __forceinline__ void populations_from(const T a[Q], T g[Q]) {
+    g[0] = a[0] - T(30) * a[1] + T(12) * a[2];
+    const T axis = a[0] - T(11) * a[1] - T(4) * a[2];
+    const T bx = axis + T(2) * a[9] - T(4) * a[10];
+    const T ox = a[3] - T(4) * a[4];
+    g[1] = bx + ox;
+    g[2] = bx - ox;
+    const T by = axis - a[9] + T(2) * a[10] + a[11] - T(2) * a[12];
+    const T oy = a[5] - T(4) * a[6];
+    g[3] = by + oy;
+    g[4] = by - oy;
+    const T bz = axis - a[9] + T(2) * a[10] - a[11] + T(2) * a[12];
+    const T oz = a[7] - T(4) * a[8];
+    g[5] = bz + oz;
+    g[6] = bz - oz;
+    const T edge = a[0] + T(8) * a[1] + a[2];
+    const T ox2 = a[3] + a[4], oy2 = a[5] + a[6], oz2 = a[7] + a[8];
+    const T bxy = edge + a[9] + a[10] + a[11] + a[12];
+    const T t1 = ox2 + oy2 + a[16] - a[17];
+    g[7] = bxy + a[13] + t1;
+    g[8] = bxy + a[13] - t1;
+    const T t2 = ox2 - oy2 + a[16] + a[17];
+    g[9] = bxy - a[13] + t2;
+    g[10] = bxy - a[13] - t2;
+    const T bxz = edge + a[9] + a[10] - a[11] - a[12];
+    const T t3 = ox2 + oz2 - a[16] + a[18];
+    g[11] = bxz + a[15] + t3;
+    g[12] = bxz + a[15] - t3;
+    const T t4 = ox2 - oz2 - a[16] - a[18];
+    g[13] = bxz - a[15] + t4;
+    g[14] = bxz - a[15] - t4;
+    const T byz = edge - T(2) * (a[9] + a[10]);
+    const T t5 = oy2 + oz2 + a[17] - a[18];
+    g[15] = byz + a[14] + t5;
+    g[16] = byz + a[14] - t5;
+    const T t6 = oy2 - oz2 + a[17] + a[18];
+    g[17] = byz - a[14] + t6;
+    g[18] = byz - a[14] - t6;
+}
+
+// Relaxation rate of moment k.
+template <typename T>
+__device__ __forceinline__ T rate_of(int k, const Collide<T> &p) {
+    return (k == 0 || k == 3 || k == 5 || k == 7) ? T(0)
+         : k == 1 ? p.se
+         : k == 2 ? p.seps
+         : (k == 4 || k == 6 || k == 8) ? p.sq
+         : (k == 10 || k == 12) ? p.spi
+         : k >= 16 ? p.sm
+                   : p.snu;
+}
+
+// Equilibrium moments (shifted: rho is the deviation) and forcing moments
+// for shifted momentum j (u = j / rho0, rho0 = 1).
+template <typename T>
+__device__ __forceinline__ void eq_and_force(T rho, T jx, T jy, T jz, const Collide<T> &p,
+                                             T meq[Q], T mF[Q]) {
+    const T q = p.linear ? T(0) : T(1);
+    const T jj = q * (jx * jx + jy * jy + jz * jz);
+    const T qxx = q * (T(2) * jx * jx - jy * jy - jz * jz);
+    const T qww = q * (jy * jy - jz * jz);
+    meq[0] = rho;
+    meq[1] = T(-11) * rho + T(19) * jj;
+    meq[2] = T(3) * rho - T(5.5) * jj;
+    meq[3] = jx;
+    meq[4] = T(-2.0 / 3.0) * jx;
+    meq[5] = jy;
+    meq[6] = T(-2.0 / 3.0) * jy;
+    meq[7] = jz;
+    meq[8] = T(-2.0 / 3.0) * jz;
+    meq[9] = qxx;
+    meq[10] = T(-0.5) * qxx;
+    meq[11] = qww;
+    meq[12] = T(-0.5) * qww;
+    meq[13] = q * jx * jy;
+    meq[14] = q * jy * jz;
+    meq[15] = q * jx * jz;
+    meq[16] = meq[17] = meq[18] = T(0);
+    const T uF = q * (jx * p.Fx + jy * p.Fy + jz * p.Fz);
+    const T fxx = q * T(2) * (T(2) * jx * p.Fx - jy * p.Fy - jz * p.Fz);
+    const T fww = q * T(2) * (jy * p.Fy - jz * p.Fz);
+    mF[0] = T(0);
+    mF[1] = T(38) * uF;
+    mF[2] = T(-11) * uF;
+    mF[3] = p.Fx;
+    mF[4] = T(-2.0 / 3.0) * p.Fx;
+    mF[5] = p.Fy;
+    mF[6] = T(-2.0 / 3.0) * p.Fy;
+    mF[7] = p.Fz;
+    mF[8] = T(-2.0 / 3.0) * p.Fz;
+    mF[9] = fxx;
+    mF[10] = T(-0.5) * fxx;
+    mF[11] = fww;
+    mF[12] = T(-0.5) * fww;
+    mF[13] = q * (jx * p.Fy + jy * p.Fx);
+    mF[14] = q * (jy * p.Fz + jz * p.Fy);
+    mF[15] = q * (jx * p.Fz + jz * p.Fx);
+    mF[16] = mF[17] = mF[18] = T(0);
+}
+
+// g <- C(g), returning the shifted momentum j of the collided state.
+template <typename T>
+__device__ __forceinline__ void mrt_collide(T g[Q], const Collide<T> &p, T &jx_out, T &jy_out,
+                                            T &jz_out) {
+    T m[Q], meq[Q], mF[Q];
+    moments_of<T>(g, m);
+    const T jx = m[3] + T(0.5) * p.Fx, jy = m[5] + T(0.5) * p.Fy, jz = m[7] + T(0.5) * p.Fz;
     jx_out = jx;
     jy_out = jy;
     jz_out = jz;
-
-    // equilibrium (quadratic part) and forcing moments in u = j / rho0
-    T jj = T(0), qxx = T(0), qww = T(0), qxy = T(0), qyz = T(0), qxz = T(0);
-    T uF = T(0), fxx = T(0), fww = T(0), fxy = T(0), fyz = T(0), fxz = T(0);
-    if (!p.linear) {
-        jj = jx * jx + jy * jy + jz * jz;
-        qxx = T(2) * jx * jx - jy * jy - jz * jz;
-        qww = jy * jy - jz * jz;
-        qxy = jx * jy;
-        qyz = jy * jz;
-        qxz = jx * jz;
-        uF = jx * p.Fx + jy * p.Fy + jz * p.Fz;
-        fxx = T(2) * (T(2) * jx * p.Fx - jy * p.Fy - jz * p.Fz);
-        fww = T(2) * (jy * p.Fy - jz * p.Fz);
-        fxy = jx * p.Fy + jy * p.Fx;
-        fyz = jy * p.Fz + jz * p.Fy;
-        fxz = jx * p.Fz + jz * p.Fx;
+    eq_and_force<T>(m[0], jx, jy, jz, p, meq, mF);
+    // m*_k = m_k - s_k (m_k - meq_k) + (1 - s_k/2) mF_k, scaled by 1/D_k
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const T s = rate_of<T>(k, p);
+        m[k] = (m[k] - s * (m[k] - meq[k]) + (T(1) - T(0.5) * s) * mF[k]) * inv_norm<T>(k);
     }
-    const T ke = T(1) - half * p.se, keps = T(1) - half * p.seps, kq = T(1) - half * p.sq;
-    const T knu = T(1) - half * p.snu, kpi = T(1) - half * p.spi;
-
-    // post-collision moments m*_k = m_k - s_k (m_k - meq_k) + (1 - s_k/2) mF_k
-    const T e_s = e - p.se * (e - (T(-11) * rho + T(19) * jj)) + ke * (T(38) * uF);
-    const T eps_s = eps - p.seps * (eps - (T(3) * rho - T(5.5) * jj)) + keps * (T(-11) * uF);
-    const T twothird = T(2.0 / 3.0);
-    const T qx_s = qx - p.sq * (qx + twothird * jx) - kq * twothird * p.Fx;
-    const T qy_s = qy - p.sq * (qy + twothird * jy) - kq * twothird * p.Fy;
-    const T qz_s = qz - p.sq * (qz + twothird * jz) - kq * twothird * p.Fz;
-    const T jx_s = jxr + p.Fx, jy_s = jyr + p.Fy, jz_s = jzr + p.Fz;
-    const T pxx_s = pxx - p.snu * (pxx - qxx) + knu * fxx;
-    const T pixx_s = pixx - p.spi * (pixx + half * qxx) - kpi * half * fxx;
-    const T pww_s = pww - p.snu * (pww - qww) + knu * fww;
-    const T piww_s = piww - p.spi * (piww + half * qww) - kpi * half * fww;
-    const T pxy_s = pxy - p.snu * (pxy - qxy) + knu * fxy;
-    const T pyz_s = pyz - p.snu * (pyz - qyz) + knu * fyz;
-    const T pxz_s = pxz - p.snu * (pxz - qxz) + knu * fxz;
-    const T km = T(1) - p.sm;
-    const T mx_s = km * mx, my_s = km * my, mz_s = km * mz;
-
-    // f* = M^T D^-1 m*, with D = (19, 2394, 252, 10, 40, 10, 40, 10, 40, 36,
-    // 72, 12, 24, 4, 4, 4, 8, 8, 8)
-    const T a0 = rho * T(1.0 / 19.0);
-    const T a1 = e_s * T(1.0 / 2394.0);
-    const T a2 = eps_s * T(1.0 / 252.0);
-    const T a3 = jx_s * T(0.1), a4 = qx_s * T(0.025);
-    const T a5 = jy_s * T(0.1), a6 = qy_s * T(0.025);
-    const T a7 = jz_s * T(0.1), a8 = qz_s * T(0.025);
-    const T a9 = pxx_s * T(1.0 / 36.0), a10 = pixx_s * T(1.0 / 72.0);
-    const T a11 = pww_s * T(1.0 / 12.0), a12 = piww_s * T(1.0 / 24.0);
-    const T a13 = pxy_s * T(0.25), a14 = pyz_s * T(0.25), a15 = pxz_s * T(0.25);
-    const T a16 = mx_s * T(0.125), a17 = my_s * T(0.125), a18 = mz_s * T(0.125);
-
-    g[0] = a0 - T(30) * a1 + T(12) * a2;
-    const T axis = a0 - T(11) * a1 - T(4) * a2;
-    const T bx = axis + T(2) * a9 - T(4) * a10;
-    const T ox = a3 - T(4) * a4;
-    g[1] = bx + ox;
-    g[2] = bx - ox;
-    const T by = axis - a9 + T(2) * a10 + a11 - T(2) * a12;
-    const T oy = a5 - T(4) * a6;
-    g[3] = by + oy;
-    g[4] = by - oy;
-    const T bz = axis - a9 + T(2) * a10 - a11 + T(2) * a12;
-    const T oz = a7 - T(4) * a8;
-    g[5] = bz + oz;
-    g[6] = bz - oz;
-
-    const T edge = a0 + T(8) * a1 + a2;
-    const T ox2 = a3 + a4, oy2 = a5 + a6, oz2 = a7 + a8;
-    const T bxy = edge + a9 + a10 + a11 + a12;
-    const T t1 = ox2 + oy2 + a16 - a17;
-    g[7] = bxy + a13 + t1;
-    g[8] = bxy + a13 - t1;
-    const T t2 = ox2 - oy2 + a16 + a17;
-    g[9] = bxy - a13 + t2;
-    g[10] = bxy - a13 - t2;
-    const T bxz = edge + a9 + a10 - a11 - a12;
-    const T t3 = ox2 + oz2 - a16 + a18;
-    g[11] = bxz + a15 + t3;
-    g[12] = bxz + a15 - t3;
-    const T t4 = ox2 - oz2 - a16 - a18;
-    g[13] = bxz - a15 + t4;
-    g[14] = bxz - a15 - t4;
-    const T byz = edge - T(2) * (a9 + a10);
-    const T t5 = oy2 + oz2 + a17 - a18;
-    g[15] = byz + a14 + t5;
-    g[16] = byz + a14 - t5;
-    const T t6 = oy2 - oz2 + a17 + a18;
-    g[17] = byz - a14 + t6;
-    g[18] = byz - a14 - t6;
+    populations_from<T>(m, g);
 }
 
 }  // namespace lbm

@@ -99,6 +99,7 @@ struct __align__(8) RowWord {
 struct SparseMap {
     const int32_t *fidx;
     const uint32_t *bb;
+    const uint2 *nb;  // per fluid node {node index, bounceback bits}: one 8-byte load
     const RowWord *rw;
     const int32_t *rstart;
     int Lx, Ly, Lz, Wr;
@@ -140,6 +141,8 @@ struct lbm_ctx {
     uint32_t *d_lw;       // [N] dense link words (AB, AA)
     int32_t *d_fidx;      // [Nf] sparse: node index of each fluid node
     uint32_t *d_bb;       // [Nf] sparse: bounceback bits
+    uint2 *d_nb;          // [Nf] sparse: {node index, bounceback bits} interleaved
+    int persist_grid;     // resident blocks of the persistent odd-step kernel
     lbm::RowWord *d_rw;   // [Ly*Lz][Wr] sparse: row fluid bits + fluid index base
     int32_t *d_rstart;    // [Ly*Lz + 1] sparse: fluid index of each row's first node
     int Wr;               // 32-voxel words per row
@@ -157,4 +160,9 @@ struct lbm_ctx {
     double *h_U;          // pinned [8*3 + 2]
     int64_t launches;
     uint8_t *h_mask;      // host copy of the mask [N]
+    int set;              // lbm_set of the rates, -1 when given directly
+    double Lambda;        // Set E magic parameter
+    bool converged;       // the stopping rule held and the state has not moved since
+    bool has_conv;        // U_conv holds the measure of a finished stopping-rule run
+    double U_conv[3];     // the mean velocity that run stopped on
 };

@@ -22,38 +22,11 @@
 //  SPARSE  the AA pattern over the fluid list, neighbours from a table.
 #include <math.h>
 
-#include "lbm_collide.cuh"
-#include "lbm_sparse.cuh"
+#include "lbm_step.cuh"
 
 namespace lbm {
 
 // ---------------------------------------------------------------- helpers
-
-struct DenseNode {
-    int x, xm, xp;
-    uint32_t row[3][3];  // Lx*(y' + Ly*z') for y' in {y-1, y, y+1}, z' likewise (wrapped)
-
-    __device__ __forceinline__ void init(uint32_t n, const Dims &d) {
-        uint32_t t = n / (uint32_t)d.Lx;
-        x = (int)(n - t * (uint32_t)d.Lx);
-        int z = (int)(t / (uint32_t)d.Ly);
-        int y = (int)(t - (uint32_t)z * (uint32_t)d.Ly);
-        xm = x == 0 ? d.Lx - 1 : x - 1;
-        xp = x == d.Lx - 1 ? 0 : x + 1;
-        int ys[3] = {y == 0 ? d.Ly - 1 : y - 1, y, y == d.Ly - 1 ? 0 : y + 1};
-        int zs[3] = {z == 0 ? d.Lz - 1 : z - 1, z, z == d.Lz - 1 ? 0 : z + 1};
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                row[a][b] = (uint32_t)d.Lx * ((uint32_t)ys[a] + (uint32_t)d.Ly * (uint32_t)zs[b]);
-    }
-    // node index of the upstream neighbour x - c_j
-    __device__ __forceinline__ uint32_t up(int j) const {
-        int xs = cx(j) > 0 ? xm : (cx(j) < 0 ? xp : x);
-        return (uint32_t)xs + row[1 - cy(j)][1 - cz(j)];
-    }
-};
 
 template <typename C>
 __device__ __forceinline__ void block_reduce_velocity(C jx, C jy, C jz, bool fluid,
@@ -114,16 +87,6 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
 
 // ------------------------------------------------------ AA, dense and sparse
 
-// Location (flat offset) of logical direction j for node n: the even pattern
-// is slot j of the node; the odd pattern is slot opp(j) of the upstream
-// neighbour, or slot j of the node when that neighbour is solid.
-template <bool ODD>
-__device__ __forceinline__ size_t aa_loc_dense(int j, uint32_t n, uint32_t w,
-                                               const DenseNode &nd, uint32_t N) {
-    if (!ODD || j == 0 || (w & (1u << j))) return (size_t)j * N + n;
-    return (size_t)opp(j) * N + nd.up(j);
-}
-
 template <typename S, bool ODD>
 __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ lw, Dims d,
                                             Collide<typename Store<S>::C> p, float ld_scale,
@@ -131,19 +94,8 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
     using C = typename Store<S>::C;
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
-    const bool fluid = !(w & SOLID_BIT);
     C jx = C(0), jy = C(0), jz = C(0);
-    if (fluid) {
-        DenseNode nd;
-        if (ODD) nd.init(n, d);
-        C g[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) g[j] = Store<S>::ld(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), ld_scale);
-        mrt_collide<C>(g, p, jx, jy, jz);
-#pragma unroll
-        for (int j = 0; j < Q; ++j)
-            Store<S>::st(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), g[opp(j)], st_scale);
-    }
+    const bool fluid = aa_dense_update<S, ODD>(A, n, w, d, p, ld_scale, st_scale, jx, jy, jz);
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
@@ -151,12 +103,16 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
 // registers per thread; more resident warps hide the odd step's dependent
 // index loads).
 #ifndef LBM_SPARSE_MIN_BLOCKS
-#define LBM_SPARSE_MIN_BLOCKS 4
+#define LBM_SPARSE_MIN_BLOCKS 3
+#endif
+#ifndef LBM_SPARSE_MIN_BLOCKS_EVEN
+#define LBM_SPARSE_MIN_BLOCKS_EVEN 3
 #endif
 
 // Idx: type of the flat population offsets; uint32_t whenever 19 * Nf < 2^32.
 template <typename S, bool ODD, typename Idx>
-__global__ void __launch_bounds__(256, LBM_SPARSE_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
+                                       : (ODD ? LBM_SPARSE_MIN_BLOCKS : LBM_SPARSE_MIN_BLOCKS_EVEN))
     k_sparse(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p, float ld_scale,
              float st_scale, Reduce red) {
     using C = typename Store<S>::C;
@@ -164,26 +120,45 @@ __global__ void __launch_bounds__(256, LBM_SPARSE_MIN_BLOCKS)
     const bool fluid = k < Nf;
     C jx = C(0), jy = C(0), jz = C(0);
     if (fluid) {
-        Idx loc[Q];
-        if (ODD) {
-            SparseNode sn;
-            sn.init(k, m);
-            loc[0] = k;
-#pragma unroll
-            for (int j = 1; j < Q; ++j)
-                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up(j, m);
-        } else {
-#pragma unroll
-            for (int j = 0; j < Q; ++j) loc[j] = (Idx)j * Nf + k;
-        }
-        C g[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) g[j] = Store<S>::ld(A + loc[j], ld_scale);
-        mrt_collide<C>(g, p, jx, jy, jz);
-#pragma unroll
-        for (int j = 0; j < Q; ++j) Store<S>::st(A + loc[j], g[opp(j)], st_scale);
+        const uint2 nb = ODD ? __ldg(m.nb + k) : make_uint2(0u, 0u);
+        aa_sparse_update<S, ODD, Idx>(A, m, Nf, k, nb, p, ld_scale, st_scale, jx, jy, jz);
     }
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
+}
+
+// Persistent odd step of the sparse layout: a grid of resident blocks walks
+// the fluid nodes k, k + stride, ...; each thread loads the next node's
+// {node index, bounceback bits} before it gathers the current node, so that
+// dependent fetch overlaps the previous node's gathers and collision instead
+// of sitting at the head of every node's latency chain.  Steps that measure
+// the mean velocity use the one-node-per-thread kernel above.
+#ifndef LBM_SPARSE_PERSISTENT
+#define LBM_SPARSE_PERSISTENT 1
+#endif
+
+template <typename S, typename Idx>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCKS)
+    k_sparse_odd_p(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
+                   float ld_scale, float st_scale) {
+    using C = typename Store<S>::C;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    uint2 nxt = k < Nf ? __ldg(m.nb + k) : make_uint2(0u, 0u);
+    for (; k < Nf; k += stride) {
+        const uint2 cur = nxt;
+        if (k + stride < Nf) nxt = __ldg(m.nb + k + stride);
+        C jx, jy, jz;
+        aa_sparse_update<S, true, Idx>(A, m, Nf, k, cur, p, ld_scale, st_scale, jx, jy, jz);
+    }
+}
+
+template <typename S, typename Idx>
+int persistent_grid_t() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_p<S, Idx>, 256, 0);
+    return sms * (per > 0 ? per : 1);
 }
 
 // ------------------------------------------------------- reduction finalise
@@ -389,6 +364,7 @@ SparseMap sparse_map(const lbm_ctx *c) {
     SparseMap m;
     m.fidx = c->d_fidx;
     m.bb = c->d_bb;
+    m.nb = c->d_nb;
     m.rw = c->d_rw;
     m.rstart = c->d_rstart;
     m.Lx = c->Lx;
@@ -438,7 +414,20 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
     default:
         grid = nblocks(c->Nf, bs);
         if (grid == 0) break;
-        if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+        if (LBM_SPARSE_PERSISTENT && odd && !reduce) {
+            const bool narrow = 19 * (uint64_t)c->Nf < (uint64_t(1) << 32);
+            if (c->persist_grid == 0)
+                c->persist_grid = narrow ? persistent_grid_t<S, uint32_t>() : persistent_grid_t<S, size_t>();
+            unsigned pg = (unsigned)c->persist_grid;
+            if (pg > grid) pg = grid;
+            if (narrow)
+                k_sparse_odd_p<S, uint32_t><<<pg, 256, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
+            else
+                k_sparse_odd_p<S, size_t><<<pg, 256, 0, c->stream>>>(
+                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
+            grid = pg;
+        } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
             if (odd)
                 k_sparse<S, true, uint32_t><<<grid, bs, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);

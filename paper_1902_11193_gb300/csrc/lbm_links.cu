@@ -172,7 +172,7 @@ __global__ void k_sparse_nbr(SparseMap m, uint32_t Nf, int32_t *nbr) {
 
 __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, int Lx, int Ly,
                                int Lz, const int32_t *__restrict__ node2fluid, uint32_t *bb,
-                               unsigned long long *links) {
+                               uint2 *nb, unsigned long long *links) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bits = 0;
     const bool valid = k < Nf;
@@ -183,6 +183,7 @@ __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, in
             if (node2fluid[upstream(n, j, Lx, Ly, Lz)] < 0) bits |= 1u << j;
         }
         bb[k] = bits;
+        nb[k] = make_uint2(n, bits);
     }
     count_links(bits, valid, links);
 }
@@ -221,7 +222,7 @@ int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
     const uint32_t Nf = (uint32_t)c->Nf;
     if (Nf > 0)
         k_sparse_links<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_fidx, Nf, c->Lx, c->Ly, c->Lz,
-                                                                 d_n2f, c->d_bb, d_links);
+                                                                 d_n2f, c->d_bb, c->d_nb, d_links);
     c->launches += 5;
     uint32_t tot = 0;
     e = cudaGetLastError();

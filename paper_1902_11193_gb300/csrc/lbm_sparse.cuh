@@ -57,9 +57,15 @@ struct SparseNode {
     int32_t rank[8];  // fluid index of the first fluid voxel at >= x in each neighbour row
 
     __device__ __forceinline__ void init(uint32_t kk, const SparseMap &m) {
+        const uint2 v = __ldg(m.nb + kk);
+        init_from(kk, v.x, v.y, m);
+    }
+
+    // n: node index of fluid node kk, b: its bounceback bits
+    __device__ __forceinline__ void init_from(uint32_t kk, uint32_t n, uint32_t b,
+                                              const SparseMap &m) {
         k = kk;
-        bits = m.bb[kk];
-        const uint32_t n = (uint32_t)m.fidx[kk];
+        bits = b;
         const uint32_t R = fast_div(n, (uint32_t)m.Lx, m.mLx);
         x = (int)(n - R * (uint32_t)m.Lx);
         z = (int)fast_div(R, (uint32_t)m.Ly, m.mLy);
@@ -78,8 +84,8 @@ struct SparseNode {
         for (int s = 0; s < 8; ++s) {
             rank[s] = 0;
             if ((bits & slot_dirs(s)) != slot_dirs(s)) {  // some upstream voxel in the row is fluid
-                const RowWord rw = m.rw[yo[1 + slot_dy(s)] + zo[1 + slot_dz(s)] + w];
-                rank[s] = rw.base + __popc(rw.bits & below);
+                const uint2 rw = __ldg(reinterpret_cast<const uint2 *>(m.rw) + (yo[1 + slot_dy(s)] + zo[1 + slot_dz(s)] + w));
+                rank[s] = (int32_t)rw.y + __popc(rw.x & below);
             }
         }
     }
@@ -99,20 +105,20 @@ struct SparseNode {
         const int dx = cx(j);
         if (cy(j) == 0 && cz(j) == 0) {  // own row
             if (dx > 0) {
-                if (xlo) return (uint32_t)(m.rstart[(uint32_t)y + (uint32_t)m.Ly * z + 1] - 1);
+                if (xlo) return (uint32_t)(__ldg(m.rstart + ((uint32_t)y + (uint32_t)m.Ly * z + 1)) - 1);
                 return k - 1;
             }
-            if (xhi) return (uint32_t)m.rstart[(uint32_t)y + (uint32_t)m.Ly * z];
+            if (xhi) return (uint32_t)__ldg(m.rstart + ((uint32_t)y + (uint32_t)m.Ly * z));
             return k + 1;
         }
         const int s = row_slot(j);
         if (dx == 0) return (uint32_t)rank[s];
         if (dx > 0) {  // upstream at x - 1
-            if (xlo) return (uint32_t)(m.rstart[nrow(m, s) + 1] - 1);
+            if (xlo) return (uint32_t)(__ldg(m.rstart + (nrow(m, s) + 1)) - 1);
             return (uint32_t)(rank[s] - 1);
         }
         // upstream at x + 1: skip (x, row) if that voxel is fluid
-        if (xhi) return (uint32_t)m.rstart[nrow(m, s)];
+        if (xhi) return (uint32_t)__ldg(m.rstart + (nrow(m, s)));
         return (uint32_t)rank[s] + ((bits >> slot_axis_dir(s)) & 1u ? 0u : 1u);
     }
 };

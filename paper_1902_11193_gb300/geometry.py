@@ -38,6 +38,8 @@ def _L():
         L.geom_duct.argtypes = [u8p, C.c_int, C.c_int, C.c_int]
         L.geom_pipe.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_double]
         L.geom_triangle.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_double]
+        L.geom_fill_isolated.argtypes = [u8p, C.c_int, C.c_int, C.c_int]
+        L.geom_fill_isolated.restype = C.c_int64
         L.geom_splitmix64.argtypes = [C.POINTER(C.c_uint64)]
         L.geom_splitmix64.restype = C.c_uint64
         for fn in ("geom_sphere_array", "geom_boolean", "geom_slit", "geom_duct",
@@ -74,15 +76,32 @@ def sphere_array(L: int, kind: str | int = "sc", r: float | None = None,
     return m
 
 
-def boolean(dims, r: float, porosity: float, seed: int, max_spheres: int = 0):
+def boolean(dims, r: float, porosity: float, seed: int, max_spheres: int = 0,
+            connected: bool = False):
     """Overlapping monodisperse spheres at SplitMix64(seed) centres until the
-    porosity is <= target.  Returns (mask, n_spheres)."""
+    porosity is <= target.  connected=True then fills enclosed pores (see
+    fill_isolated).  Returns (mask, n_spheres)."""
     Lx, Ly, Lz = (dims, dims, dims) if np.isscalar(dims) else dims
     m = np.zeros((Lz, Ly, Lx), np.uint8)
     ns, nsol = C.c_int64(0), C.c_int64(0)
     _check(_L().geom_boolean(m, Lx, Ly, Lz, float(r), float(porosity), C.c_uint64(seed),
                              int(max_spheres), C.byref(ns), C.byref(nsol)))
+    if connected:
+        fill_isolated(m)
     return m, int(ns.value)
+
+
+def fill_isolated(mask: np.ndarray) -> int:
+    """In place: fills as solid every fluid cluster except the largest, with
+    clusters joined by D3Q19 links under periodic wrap (the usual removal of
+    enclosed pores from a segmented image).  Returns the voxels filled."""
+    if not (mask.flags.c_contiguous and mask.dtype == np.uint8):
+        raise ValueError("mask must be a C-contiguous uint8 array")
+    Lz, Ly, Lx = mask.shape
+    n = int(_L().geom_fill_isolated(mask, Lx, Ly, Lz))
+    if n < 0:
+        raise ValueError("fill_isolated failed")
+    return n
 
 
 def slit(H: int, W: int = 1, Lx: int = 1, Lz: int = 1) -> np.ndarray:

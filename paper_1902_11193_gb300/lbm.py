@@ -37,10 +37,32 @@ class LBMError(RuntimeError):
         self.code = code
 
 
+class Grad(C.Structure):
+    _fields_ = [("dk_dtau", C.c_double), ("dk_dLambda", C.c_double),
+                ("dk_dLambda_q", C.c_double), ("dk_dLambda_m", C.c_double),
+                ("dk_dF", C.c_double * 3), ("dk_ds", C.c_double * 6), ("k", C.c_double),
+                ("iterations", C.c_int64), ("residual", C.c_double)]
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("mask", C.c_void_p), ("dims", C.c_int32 * 3), ("set", C.c_int32),
+                ("tau", C.c_double), ("Lambda", C.c_double), ("s", C.c_double * 19),
+                ("force", C.c_double * 3)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("nodes_per_thread", C.c_int32),
+                ("check_interval", C.c_int32), ("linear_eq", C.c_int32), ("max_steps", C.c_int64),
+                ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
+                ("barrier_timeout_ms", C.c_int32), ("test_skip_block", C.c_int32),
+                ("stop_rule", C.c_int32)]
+
+
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("check_interval", C.c_int32),
                 ("linear_eq", C.c_int32), ("max_steps", C.c_int64), ("cuda_stream", C.c_void_p),
-                ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32)]
+                ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32),
+                ("stop_rule", C.c_int32)]
 
 
 _lib = None
@@ -79,6 +101,19 @@ def lib():
             "lbm_kernel_launches": (i64, [vp]),
             "lbm_save": (C.c_int, [vp, C.c_char_p]),
             "lbm_load": (C.c_int, [C.POINTER(vp), C.c_char_p, C.POINTER(Options)]),
+            "lbm_adjoint": (C.c_int, [vp, dbl, i64, C.POINTER(Grad)]),
+            "lbm_converged_velocity": (C.c_int, [vp, dp]),
+            "lbm_converged_permeability": (C.c_int, [vp, dp]),
+            "lbm_batch_default_options": (None, [C.POINTER(BatchOptions)]),
+            "lbm_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(LatticeDesc),
+                                           C.POINTER(BatchOptions)]),
+            "lbm_batch_run": (C.c_int, [vp, dbl, vp, vp]),
+            "lbm_batch_permeability": (C.c_int, [vp, vp]),
+            "lbm_batch_mean_velocity": (C.c_int, [vp, vp]),
+            "lbm_batch_config": (C.c_int, [vp, vp, vp]),
+            "lbm_batch_lattice": (vp, [vp, i32]),
+            "lbm_batch_kernel_launches": (i64, [vp]),
+            "lbm_batch_destroy": (None, [vp]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_last_cuda_error": (C.c_char_p, []),
         }
@@ -120,7 +155,7 @@ class LBMSolver:
     def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
                  rates_=None, precision="fp32", layout="aa", check_interval=100,
                  linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
-                 block_size=0):
+                 block_size=0, stop_rule=0):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         if self.mask.ndim != 3:
             raise ValueError("mask must be [Lz, Ly, Lx]")
@@ -135,6 +170,7 @@ class LBMSolver:
         o.max_steps = int(max_steps)
         o.fp16_scale_log2 = int(fp16_scale_log2)
         o.block_size = int(block_size)
+        o.stop_rule = int(stop_rule)
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self.options = o
@@ -173,7 +209,8 @@ class LBMSolver:
 
     def close(self) -> None:
         if getattr(self, "_h", None):
-            lib().lbm_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib().lbm_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -209,6 +246,17 @@ class LBMSolver:
     def permeability(self) -> np.ndarray:
         k = np.zeros(3)
         _check(lib().lbm_permeability(self._h, k), "lbm_permeability")
+        return k
+
+    def converged_velocity(self) -> np.ndarray:
+        """The mean velocity the last stopping-rule run stopped on."""
+        U = np.zeros(3)
+        _check(lib().lbm_converged_velocity(self._h, U), "lbm_converged_velocity")
+        return U
+
+    def converged_permeability(self) -> np.ndarray:
+        k = np.zeros(3)
+        _check(lib().lbm_converged_permeability(self._h, k), "lbm_converged_permeability")
         return k
 
     def velocity(self) -> np.ndarray:
@@ -260,3 +308,114 @@ class LBMSolver:
 
     def save(self, path: str) -> None:
         _check(lib().lbm_save(self._h, path.encode()), "lbm_save")
+
+    def adjoint(self, tol: float = 1e-8, max_iter: int = 1_000_000) -> dict:
+        """Gradient of the converged permeability along the drive (lbm_adjoint)."""
+        g = Grad()
+        _check(lib().lbm_adjoint(self._h, float(tol), int(max_iter), C.byref(g)), "lbm_adjoint")
+        return {"dtau": g.dk_dtau, "dLambda": g.dk_dLambda, "dLambda_q": g.dk_dLambda_q,
+                "dLambda_m": g.dk_dLambda_m, "dF": np.array(list(g.dk_dF)),
+                "ds": np.array(list(g.dk_ds)), "k": g.k, "iterations": int(g.iterations),
+                "residual": g.residual}
+
+
+class LBMBatch:
+    """Many lattices stepped together by the batched persistent kernel
+    (lbm_batch_*).  `lattices` is a list of dicts with keys mask, and either
+    set_/tau/Lambda or rates_, and force.  layout None lets the autotuner pick
+    dense AA or sparse per distinct image; nodes_per_thread 0 likewise."""
+
+    def __init__(self, lattices, precision="fp32", layout=None, nodes_per_thread=0,
+                 check_interval=100, linear_eq=False, max_steps=1_000_000, stream=None,
+                 use_graph=True, barrier_timeout_ms=2000, test_skip_block=-1, stop_rule=0):
+        self.masks = [np.ascontiguousarray(l["mask"], np.uint8) for l in lattices]
+        n = len(lattices)
+        descs = (LatticeDesc * n)()
+        for i, (l, m) in enumerate(zip(lattices, self.masks)):
+            d = descs[i]
+            d.mask = m.ctypes.data
+            for a, v in enumerate(m.shape[::-1]):
+                d.dims[a] = v
+            if l.get("rates_") is not None:
+                d.set = -1
+                for k, v in enumerate(np.asarray(l["rates_"], np.float64)):
+                    d.s[k] = v
+            else:
+                st = l.get("set_", "B")
+                d.set = SET_NAMES[st] if isinstance(st, str) else int(st)
+                d.tau = float(l.get("tau", 1.0))
+                d.Lambda = float(l.get("Lambda", 3.0 / 16.0))
+            for a, v in enumerate(l.get("force", (1e-6, 0.0, 0.0))):
+                d.force[a] = float(v)
+        o = BatchOptions()
+        lib().lbm_batch_default_options(C.byref(o))
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.layout = -1 if layout is None else (LAYOUTS[layout] if isinstance(layout, str) else int(layout))
+        o.nodes_per_thread = int(nodes_per_thread)
+        o.check_interval = int(check_interval)
+        o.linear_eq = int(bool(linear_eq))
+        o.max_steps = int(max_steps)
+        o.use_graph = int(bool(use_graph))
+        o.barrier_timeout_ms = int(barrier_timeout_ms)
+        o.test_skip_block = int(test_skip_block)
+        o.stop_rule = int(stop_rule)
+        if stream is not None:
+            o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        h = C.c_void_p()
+        _check(lib().lbm_batch_create(C.byref(h), n, descs, C.byref(o)), "lbm_batch_create")
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, tol: float, raise_on_failure: bool = True):
+        """Returns (steps[n], status[n])."""
+        steps = np.zeros(self.n, np.int64)
+        status = np.zeros(self.n, np.int32)
+        rc = lib().lbm_batch_run(self._h, float(tol), steps.ctypes.data, status.ctypes.data)
+        if rc != 0 and raise_on_failure:
+            raise LBMError(rc, "lbm_batch_run")
+        return (steps, status) if rc == 0 else rc
+
+    def permeability(self) -> np.ndarray:
+        k = np.zeros((self.n, 3))
+        _check(lib().lbm_batch_permeability(self._h, k.ctypes.data), "lbm_batch_permeability")
+        return k
+
+    def mean_velocity(self) -> np.ndarray:
+        U = np.zeros((self.n, 3))
+        _check(lib().lbm_batch_mean_velocity(self._h, U.ctypes.data), "lbm_batch_mean_velocity")
+        return U
+
+    def config(self):
+        lay = np.zeros(self.n, np.int32)
+        npt = np.zeros(self.n, np.int32)
+        _check(lib().lbm_batch_config(self._h, lay.ctypes.data, npt.ctypes.data), "lbm_batch_config")
+        return lay, npt
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().lbm_batch_kernel_launches(self._h))
+
+    def lattice(self, i: int) -> "LBMSolver":
+        """Non-owning view of lattice i as a single-lattice solver."""
+        h = lib().lbm_batch_lattice(self._h, int(i))
+        if not h:
+            raise IndexError(i)
+        view = LBMSolver.__new__(LBMSolver)
+        view._h = C.c_void_p(h)
+        view._owned = False  # the batch owns the context
+        view.mask = self.masks[i]
+        view.dims = np.array(self.masks[i].shape[::-1], np.int32)
+        view.N = int(self.masks[i].size)
+        view._batch = self
+        return view

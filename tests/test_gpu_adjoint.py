@@ -1,0 +1,180 @@
+"""The CUDA steady-state adjoint (lbm_adjoint) against the oracle's adjoint and
+against central finite differences of the converged permeability.
+
+Gradients are compared normalised: tau dk/dtau / k, Lambda dk/dLambda / k,
+F dk/dF / k.  FP64 GPU vs FP64 oracle adjoint: 1e-7 (both are accurate to
+~1e-8: the oracle differences the rate formulas in tau with step 1e-5).
+FP32 forward + adjoint vs FP64 finite differences (step 1e-4, forward solves
+converged to 1e-13 per step): 1e-4, the stated target.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+F1 = (1e-5, 0.0, 0.0)
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_11193_gb300 import lbm
+
+    lbm.lib()
+    return lbm
+
+
+def _norm(g, k, tau, lam, F):
+    return {"dtau": g["dtau"] * tau / k, "dLambda": g["dLambda"] * lam / k,
+            "dLambda_q": g["dLambda_q"] * (3 / 16) / k, "dLambda_m": g["dLambda_m"] * (3 / 8) / k,
+            "dF": g["dF"][0] * F[0] / k}
+
+
+def _ora_grad(ora, mask, st, tau, lam, F, linear=False):
+    O = ora.Solver(mask, ora.rates(st, tau, lam), F, linear=linear)
+    rc, _, U = O.run_to_convergence(1e-15, K=10, max_steps=60000)
+    assert rc == 0
+    k = (tau - 0.5) / 3 * U[0] / F[0]
+    rc, g, _ = O.adjoint(st, tau, lam, tol=1e-12)
+    assert rc == 0
+    g = dict(g, dF=np.array([g["dFx"], g["dFy"], g["dFz"]]))
+    return k, g
+
+
+def _gpu_grad(L, mask, st, tau, lam, F, precision="fp64", layout="ab", tol=1e-15, atol=1e-12,
+              linear=False, rule=0):
+    S = L.LBMSolver(mask, st, tau, lam, F, precision=precision, layout=layout, check_interval=10,
+                    max_steps=100000, linear_eq=linear, stop_rule=rule)
+    rc, steps = S.run_to_convergence(tol)
+    assert rc == 0, (precision, tol, steps)
+    g = S.adjoint(atol, max_iter=100000)
+    assert g["residual"] <= atol, (precision, g["residual"], g["iterations"])
+    return g["k"], g, S
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa", "sparse"])
+@pytest.mark.parametrize("st,lam", [("E", 3 / 8), ("D", 3 / 16), ("A", 3 / 16), ("SRT", 3 / 16),
+                                    ("C", 3 / 16)])
+def test_fp64_adjoint_matches_oracle(L, ora, geom, layout, st, lam):
+    mask = geom.sphere_array(10, "bcc", r=3.2)
+    tau = 0.9
+    ko, go = _ora_grad(ora, mask, st, tau, lam, F1)
+    kg, gg, _ = _gpu_grad(L, mask, st, tau, lam, F1, layout=layout)
+    assert abs(kg - ko) <= 1e-10 * abs(ko)
+    no, ng = _norm(go, ko, tau, lam, F1), _norm(gg, kg, tau, lam, F1)
+    for key in ("dtau", "dF"):
+        assert abs(ng[key] - no[key]) < 1e-7, (key, ng[key], no[key])
+    for key in ("dLambda", "dLambda_q", "dLambda_m"):
+        if st in ("B", "D", "E"):
+            assert abs(ng[key] - no[key]) < 1e-7, (key, ng[key], no[key])
+        else:
+            assert np.isnan(ng[key]) and np.isnan(no[key])
+    assert np.abs(gg["dF"][1:]).max() < 1e-6 * abs(kg / F1[0])
+
+
+def test_adjoint_state_errors(L, geom):
+    mask = geom.sphere_array(10, "bcc", r=3.2)
+    S = L.LBMSolver(mask, "B", 1.0, force=F1)
+    with pytest.raises(L.LBMError) as e:
+        S.adjoint()
+    assert e.value.code == -7  # ENOSTATE: not converged
+    S.run_to_convergence(1e-8)
+    S.step(1)
+    with pytest.raises(L.LBMError) as e:
+        S.adjoint()
+    assert e.value.code == -7
+    Z = L.LBMSolver(mask, "B", 1.0, force=(0.0, 0.0, 0.0), check_interval=2, max_steps=10)
+    Z.run_to_convergence(1e-3)
+    with pytest.raises(L.LBMError) as e:
+        Z.adjoint()
+    assert e.value.code in (-1, -7)
+
+
+@pytest.fixture(scope="module")
+def boolean48(geom):
+    """48^3 Boolean medium, sphere radius 6, porosity 0.35.  Its one- and
+    two-voxel gaps carry bounceback modes of eigenvalue near -1, so every
+    solve on it uses the two-step-mean stopping rule."""
+    return geom.boolean(48, 6, 0.35, seed=1902_11193 + 4)[0]
+
+
+def _fd(L, mask, st, tau, lam, F, which, h=1e-4):
+    """Central difference of the FP64 permeability at the fixed point (the
+    two-step mean the stopping rule converged on, to 1e-12)."""
+    def k_at(t, l, Fv):
+        S = L.LBMSolver(mask, st, t, l, Fv, precision="fp64", layout="sparse", check_interval=20,
+                        max_steps=100000, stop_rule=1)
+        rc, _ = S.run_to_convergence(1e-12)
+        assert rc == 0
+        return S.converged_permeability()[0]
+    if which == "dtau":
+        return (k_at(tau + h, lam, F) - k_at(tau - h, lam, F)) / (2 * h)
+    if which == "dLambda":
+        return (k_at(tau, lam + h, F) - k_at(tau, lam - h, F)) / (2 * h)
+    Fp, Fm = (F[0] * (1 + h), 0, 0), (F[0] * (1 - h), 0, 0)
+    return (k_at(tau, lam, Fp) - k_at(tau, lam, Fm)) / (2 * h * F[0])
+
+
+@pytest.mark.parametrize("st,lam,tau", [("B", 3 / 16, 0.8), ("D", 3 / 16, 1.3), ("E", 3 / 8, 1.0)])
+def test_fp32_adjoint_vs_finite_differences_48(L, boolean48, st, lam, tau):
+    F = (1e-6, 0.0, 0.0)
+    k, g, S = _gpu_grad(L, boolean48, st, tau, lam, F, precision="fp32", layout="sparse", tol=1e-8,
+                        atol=1e-6, rule=1)
+    checks = ["dtau", "dF"] + (["dLambda"] if st == "E" else [])
+    for key in checks:
+        fd = _fd(L, boolean48, st, tau, lam, F, key)
+        scale = {"dtau": tau, "dLambda": lam, "dF": F[0]}[key]
+        adj = g["dF"][0] if key == "dF" else g[key]
+        err = abs(adj * scale / k - fd * scale / k)
+        print(f"{st} tau={tau} {key}: adjoint {adj * scale / k:+.6e} fd {fd * scale / k:+.6e}"
+              f" err {err:.2e}")
+        assert err < 1e-4
+
+
+def test_adjoint_boolean_vs_oracle(L, ora, geom):
+    """32^3 Boolean medium (r = 4, porosity 0.35): the CPU adjoint stays within
+    a minute; FP64 and FP32 GPU adjoints against it."""
+    mask = geom.boolean(32, 4, 0.35, seed=1902_11193 + 4)[0]
+    st, tau, lam = "D", 1.0, 3 / 16
+    F = (1e-6, 0.0, 0.0)
+    O = ora.Solver(mask, ora.rates(st, tau, lam), F)
+    rc, _, U = O.run_to_convergence(1e-11, K=10, max_steps=60000, rule=1)
+    assert rc == 0
+    rc, go, _ = O.adjoint(st, tau, lam, tol=1e-9, max_iter=60000)
+    assert rc == 0
+    go = dict(go, dF=np.array([go["dFx"], go["dFy"], go["dFz"]]))
+    ko = (tau - 0.5) / 3 * U[0] / F[0]
+    no = _norm(go, ko, tau, lam, F)
+    kg, gg, _ = _gpu_grad(L, mask, st, tau, lam, F, precision="fp64", layout="sparse", tol=1e-11,
+                          atol=1e-9, rule=1)
+    ng = _norm(gg, kg, tau, lam, F)
+    k3, g3, _ = _gpu_grad(L, mask, st, tau, lam, F, precision="fp32", layout="sparse",
+                          tol=1e-8, atol=1e-6, rule=1)
+    n3 = _norm(g3, k3, tau, lam, F)
+    assert abs(kg - ko) <= 1e-9 * abs(ko)
+    for key in ("dtau", "dLambda_q", "dLambda_m", "dF"):
+        print(f"{key}: oracle {no[key]:+.8e} fp64 {ng[key]:+.8e} fp32 {n3[key]:+.8e}")
+        assert abs(ng[key] - no[key]) < 1e-6
+        assert abs(n3[key] - no[key]) < 1e-4
+
+
+def test_autograd_function(L, geom):
+    import torch
+
+    from paper_1902_11193_gb300.autograd import permeability
+
+    mask = geom.sphere_array(10, "bcc", r=3.2)
+    tau = torch.tensor(0.9, dtype=torch.float64, requires_grad=True)
+    lam = torch.tensor(3 / 8, dtype=torch.float64, requires_grad=True)
+    F = torch.tensor(F1, dtype=torch.float64, requires_grad=True)
+    k = permeability(mask, tau, lam, F, set_="E", tol=1e-14, adjoint_tol=1e-12,
+                     precision="fp64", check_interval=10)
+    k.backward()
+    _, g, _ = _gpu_grad(L, mask, "E", 0.9, 3 / 8, F1)
+    assert abs(k.item() - g["k"]) <= 1e-12 * abs(g["k"])
+    assert abs(tau.grad.item() - g["dtau"]) <= 1e-9 * abs(g["k"])
+    assert abs(lam.grad.item() - g["dLambda"]) <= 1e-9 * abs(g["dLambda"]) + 1e-12
+    assert np.allclose(F.grad.numpy(), g["dF"], rtol=1e-9, atol=1e-6)
