@@ -154,6 +154,30 @@ int lbm_set_populations(lbm_ctx *ctx, const double *f);
  * index outside [0, N). */
 int lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t count, double *f);
 
+/* Largest lattice (nodes) lbm_mean_velocity_noalloc accepts: 2^24, e.g. 256^3. */
+#define LBM_NOALLOC_MAX_NODES 16777216
+
+/* Mean velocity of a caller-held population array, without allocating any
+ * device memory.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc where they need the measurement (device memory
+ * owned by another allocator that must not be bypassed, or a loop that must
+ * not take cudaMalloc's implicit device synchronisation).
+ *   f_dev    device, FP64 [19][N]: post-collision populations of the last
+ *            step minus w_i (two-array layout: population i of node n at
+ *            i*N + n), as the FP64 AB layout keeps them
+ *   mask_dev device, uint8 [N], 1 = solid
+ *   U_dev    device, double[3]: receives the streamed-state mean velocity
+ *            (as lbm_mean_velocity: halfway bounceback, F/2 shift, over all N)
+ *   cuda_stream  stream to run on (NULL: the legacy default stream)
+ * Asynchronous on the stream.  Its scratch is a file-scope device array that
+ * every GPU loading the library keeps until exit (1.5 MiB); the first call
+ * on a device looks up the array's address (cudaGetSymbolAddress) with that
+ * device current, so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race.  LBM_EINVAL for
+ * a NULL pointer, dims <= 0, or more than LBM_NOALLOC_MAX_NODES nodes. */
+int lbm_mean_velocity_noalloc(const double *f_dev, const uint8_t *mask_dev, const int32_t dims[3],
+                              const double force[3], double *U_dev, void *cuda_stream);
+
 /* Fluid-node count and per-direction bounceback link counts (links[i] =
  * number of fluid nodes x whose upstream neighbour x - c_i is solid). */
 int lbm_link_counts(lbm_ctx *ctx, int64_t *n_fluid, int64_t links[19]);

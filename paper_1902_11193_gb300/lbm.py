@@ -102,6 +102,7 @@ def lib():
             "lbm_save": (C.c_int, [vp, C.c_char_p]),
             "lbm_load": (C.c_int, [C.POINTER(vp), C.c_char_p, C.POINTER(Options)]),
             "lbm_adjoint": (C.c_int, [vp, dbl, i64, C.POINTER(Grad)]),
+            "lbm_mean_velocity_noalloc": (C.c_int, [vp, vp, i32p, dp, vp, vp]),
             "lbm_converged_velocity": (C.c_int, [vp, dp]),
             "lbm_converged_permeability": (C.c_int, [vp, dp]),
             "lbm_batch_default_options": (None, [C.POINTER(BatchOptions)]),
