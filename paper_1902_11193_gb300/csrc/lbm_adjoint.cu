@@ -308,18 +308,7 @@ static AdjView make_adj_view(const lbm_ctx *c) {
 
 template <typename T>
 static Collide<T> collide_params(const lbm_ctx *c) {
-    Collide<T> p;
-    p.se = (T)c->s[1];
-    p.seps = (T)c->s[2];
-    p.sq = (T)c->s[4];
-    p.snu = (T)c->s[9];
-    p.spi = (T)c->s[10];
-    p.sm = (T)c->s[16];
-    p.Fx = (T)c->F[0];
-    p.Fy = (T)c->F[1];
-    p.Fz = (T)c->F[2];
-    p.linear = c->opt.linear_eq;
-    return p;
+    return make_collide<T>(c->s, c->F, c->opt.linear_eq);
 }
 
 int launch_step(lbm_ctx *c, bool reduce);

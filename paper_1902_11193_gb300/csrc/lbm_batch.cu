@@ -8,17 +8,21 @@
 // steps (each lattice's AA step t+1 reads what step t wrote).  The barrier
 // waits are bounded in time: on expiry the kernel raises an error flag and
 // returns, and the host reports LBM_ETIMEOUT.  In the last two steps of a
-// chunk each tile adds its lattice's shifted velocity to FP64 partials, a
-// per-lattice kernel sums them in a fixed order, and the host applies each
-// lattice's stopping rule and retires converged lattices from the table.
+// chunk (three under the two-step-mean rule) every 256-unit group of a tile
+// reduces its shifted velocity into an FP64 partial exactly as a
+// single-lattice block does, a per-lattice kernel sums the partials in the
+// single-lattice finalize's order, and the host applies each lattice's
+// stopping rule and retires converged lattices from the table.
 // The chunk (step-count upload, persistent kernel, reductions, result copy)
 // is captured once in a CUDA graph and replayed; the tile table lives in
 // device memory, so retiring lattices does not change the graph.
 // Every lattice is an ordinary lbm_ctx (its own populations and link
 // tables), so all single-lattice readers work on batch members, and the
 // per-unit update is the same code as the single-lattice kernels
-// (lbm_step.cuh): a batch member's state is bitwise the state of the same
-// lattice run alone with the same check interval.
+// (lbm_step.cuh) with the same explicitly rounded collision: a batch
+// member's state, step count and measured mean velocity are bitwise those of
+// the same lattice run alone with the same check interval and the default
+// 256-thread blocks.
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -43,11 +47,19 @@ struct BatchLat {
     const uint32_t *lw;
     SparseMap sm;
     Dims d;
-    double s6[6];  // se, seps, sq, snu, spi, sm
-    double F[3];
-    int linear;
+    Collide<float> pf;  // collision parameters, built like the single-lattice ones
+    Collide<double> pd;
     double inv_N;
 };
+
+template <typename C>
+__device__ __forceinline__ const Collide<C> &lat_params(const BatchLat &L);
+template <>
+__device__ __forceinline__ const Collide<float> &lat_params<float>(const BatchLat &L) { return L.pf; }
+template <>
+__device__ __forceinline__ const Collide<double> &lat_params<double>(const BatchLat &L) { return L.pd; }
+
+constexpr uint32_t kTileThreads = 256;  // threads per block of k_batch
 
 struct Tile {
     int lat;
@@ -115,89 +127,95 @@ __global__ void __launch_bounds__(256) k_batch(const BatchLat *__restrict__ lats
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const Tile tl = tiles[t];
             const BatchLat &L = lats[tl.lat];
-            Collide<C> p;
-            p.se = (C)L.s6[0];
-            p.seps = (C)L.s6[1];
-            p.sq = (C)L.s6[2];
-            p.snu = (C)L.s6[3];
-            p.spi = (C)L.s6[4];
-            p.sm = (C)L.s6[5];
-            p.Fx = (C)L.F[0];
-            p.Fy = (C)L.F[1];
-            p.Fz = (C)L.F[2];
-            p.linear = L.linear;
+            const Collide<C> &p = lat_params<C>(L);
             const bool odd = ((lat_steps[tl.lat] + s) & 1) != 0;
-            double acc[3] = {0.0, 0.0, 0.0};
+            S *A = (S *)L.pop;
             for (int r = 0; r < L.npt; ++r) {
-                const uint32_t u = tl.first + (uint32_t)r * blockDim.x + threadIdx.x;
-                if (u >= L.units) break;
+                // sub-tile r: units first + 256 r .. first + 256 r + 255, the
+                // same 256-unit group a single-lattice block covers
+                const uint32_t u0 = tl.first + (uint32_t)r * blockDim.x;
+                if (u0 >= L.units) break;  // block-uniform
+                const uint32_t u = u0 + threadIdx.x;
                 C jx = C(0), jy = C(0), jz = C(0);
-                bool fl = true;
-                S *A = (S *)L.pop;
-                if (L.layout == LBM_LAYOUT_SPARSE) {
-                    if (odd)
-                        aa_sparse_update<S, true, size_t>(A, L.sm, L.units, u, __ldg(L.sm.nb + u), p,
-                                                          1.f, 1.f, jx, jy, jz);
-                    else
-                        aa_sparse_update<S, false, size_t>(A, L.sm, L.units, u, make_uint2(0u, 0u),
-                                                           p, 1.f, 1.f, jx, jy, jz);
-                } else {
-                    const uint32_t w = L.lw[u];
-                    fl = odd ? aa_dense_update<S, true>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz)
-                             : aa_dense_update<S, false>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz);
+                bool fl = false;
+                if (u < L.units) {
+                    // populations go through L2 only: other blocks wrote them
+                    // in earlier steps of this launch (the index data is
+                    // read-only)
+                    if (L.layout == LBM_LAYOUT_SPARSE) {
+                        fl = true;
+                        if (odd)
+                            aa_sparse_update<S, true, size_t, StoreL2<S>>(
+                                A, L.sm, L.units, u, __ldg(L.sm.nb + u), p, 1.f, 1.f, jx, jy, jz);
+                        else
+                            aa_sparse_update<S, false, size_t, StoreL2<S>>(
+                                A, L.sm, L.units, u, make_uint2(0u, 0u), p, 1.f, 1.f, jx, jy, jz);
+                    } else {
+                        const uint32_t w = L.lw[u];
+                        fl = odd ? aa_dense_update<S, true, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz)
+                                 : aa_dense_update<S, false, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz);
+                    }
                 }
-                if (slot >= 0 && fl) {
-                    acc[0] += (double)jx;
-                    acc[1] += (double)jy;
-                    acc[2] += (double)jz;
+                if (slot >= 0) {
+                    // the single-lattice block reduction, term for term
+                    double v[3] = {fl ? (double)jx : 0.0, fl ? (double)jy : 0.0,
+                                   fl ? (double)jz : 0.0};
+                    __shared__ double sm[32][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+                    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) sm[threadIdx.x >> 5][a] = v[a];
+                    __syncthreads();
+                    if (threadIdx.x < 3) {
+                        double acc = 0.0;
+                        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += sm[w][threadIdx.x];
+                        tile_part[((size_t)slot * 2 * max_tiles + 2 * (size_t)t + r) * 3 + threadIdx.x] = acc;
+                    }
+                    __syncthreads();
                 }
-            }
-            if (slot >= 0) {
-                __shared__ double sm[32][3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o);
-                if ((threadIdx.x & 31) == 0)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) sm[threadIdx.x >> 5][a] = acc[a];
-                __syncthreads();
-                if (threadIdx.x < 3) {
-                    double v = 0.0;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sm[w][threadIdx.x];
-                    tile_part[((size_t)slot * max_tiles + t) * 3 + threadIdx.x] = v;
-                }
-                __syncthreads();
             }
         }
         if (s + 1 < nsteps && !grid_sync(bar, gridDim.x, timeout_ns, s == 0 && skip_me)) return;
     }
 }
 
-// U[i][slot][a] = (sum over lattice i's tiles, in tile order) / N_i, for the
-// three measurement slots.
-__global__ void __launch_bounds__(256) k_batch_finalize(const BatchLat *__restrict__ lats,
-                                                        const int2 *__restrict__ lat_tiles,
-                                                        const double *__restrict__ tile_part,
-                                                        int max_tiles, double *U) {
+// U[i][slot][a] = (sum of lattice i's 256-unit partials) / N_i for the three
+// measurement slots, in the order the single-lattice finalize uses: thread t
+// adds partials t, t + 1024, ... in order, then a fixed shared-memory tree.
+// Partial b of lattice i (units 256 b ..) sits in sub-tile b % npt of the
+// lattice's tile b / npt.
+__global__ void __launch_bounds__(1024) k_batch_finalize(const BatchLat *__restrict__ lats,
+                                                         const int2 *__restrict__ lat_tiles,
+                                                         const double *__restrict__ tile_part,
+                                                         int max_tiles, double *U) {
     const int i = blockIdx.x;
     const int2 rng = lat_tiles[i];
-    __shared__ double sm[9][256];
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = threadIdx.x; t < rng.y; t += blockDim.x)
+    const int npt = lats[i].npt;
+    const int nblk = rng.y > 0 ? (int)((lats[i].units + kTileThreads - 1) / kTileThreads) : 0;
+    __shared__ double sm[3][1024];
+    for (int slot = 0; slot < 3; ++slot) {
+        const double *part = tile_part + (size_t)slot * 2 * max_tiles * 3;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+            const size_t at = 2 * (size_t)(rng.x + b / npt) + b % npt;
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            acc[q] += tile_part[((size_t)(q / 3) * max_tiles + rng.x + t) * 3 + (q % 3)];
+            for (int a = 0; a < 3; ++a) acc[a] += part[3 * at + a];
+        }
 #pragma unroll
-    for (int q = 0; q < 9; ++q) sm[q][threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
+        for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] = acc[a];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
 #pragma unroll
-            for (int q = 0; q < 9; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+                for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] += sm[a][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x < 3) U[(size_t)9 * i + 3 * slot + threadIdx.x] = sm[threadIdx.x][0] * lats[i].inv_N;
         __syncthreads();
     }
-    if (threadIdx.x < 9) U[(size_t)9 * i + threadIdx.x] = sm[threadIdx.x][0] * lats[i].inv_N;
 }
 
 }  // namespace lbm
@@ -283,15 +301,13 @@ BatchLat make_lat(const lbm_ctx *c, int npt) {
     L.lw = c->d_lw;
     if (c->opt.layout == LBM_LAYOUT_SPARSE) L.sm = sparse_map(c);
     L.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
-    const int ks[6] = {1, 2, 4, 9, 10, 16};
-    for (int q = 0; q < 6; ++q) L.s6[q] = c->s[ks[q]];
-    for (int a = 0; a < 3; ++a) L.F[a] = c->F[a];
-    L.linear = c->opt.linear_eq;
+    L.pf = make_collide<float>(c->s, c->F, c->opt.linear_eq);
+    L.pd = make_collide<double>(c->s, c->F, c->opt.linear_eq);
     L.inv_N = 1.0 / (double)c->N;
     return L;
 }
 
-int ntiles_of(const BatchLat &L) { return (int)((L.units + 256u * L.npt - 1) / (256u * L.npt)); }
+int ntiles_of(const BatchLat &L) { return (int)((L.units + kTileThreads * L.npt - 1) / (kTileThreads * L.npt)); }
 
 int coop_grid(int precision) {
     int dev = 0, sms = 0, per = 0;
@@ -312,7 +328,7 @@ cudaError_t upload_tiles(lbm_batch *b, const std::vector<BatchLat> &lats) {
         if (!b->active[i]) continue;
         const int nt = ntiles_of(lats[i]);
         ranges[i] = make_int2((int)tiles.size(), nt);
-        for (int t = 0; t < nt; ++t) tiles.push_back(Tile{i, (uint32_t)t * 256u * lats[i].npt});
+        for (int t = 0; t < nt; ++t) tiles.push_back(Tile{i, (uint32_t)t * kTileThreads * lats[i].npt});
     }
     const int nt = (int)tiles.size();
     cudaError_t e = cudaSuccess;
@@ -335,9 +351,9 @@ cudaError_t enqueue_chunk(lbm_batch *b) {
                     &b->d_tile_part, &b->max_tiles, &b->d_bar, &b->timeout_ns};
     const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
                                                   : (const void *)k_batch<float>;
-    e = cudaLaunchCooperativeKernel(fn, dim3(b->grid), dim3(256), args, 0, b->stream);
+    e = cudaLaunchCooperativeKernel(fn, dim3(b->grid), dim3(kTileThreads), args, 0, b->stream);
     if (e != cudaSuccess) return e;
-    k_batch_finalize<<<b->n, 256, 0, b->stream>>>(b->d_lats, b->d_lat_tiles, b->d_tile_part,
+    k_batch_finalize<<<b->n, 1024, 0, b->stream>>>(b->d_lats, b->d_lat_tiles, b->d_tile_part,
                                                   b->max_tiles, b->d_U);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -352,7 +368,7 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
     BatchLat L = make_lat(c, npt);
     const int nt = ntiles_of(L);
     std::vector<Tile> tiles;
-    for (int t = 0; t < nt; ++t) tiles.push_back(Tile{0, (uint32_t)t * 256u * npt});
+    for (int t = 0; t < nt; ++t) tiles.push_back(Tile{0, (uint32_t)t * kTileThreads * npt});
     BatchLat *d_l = nullptr;
     Tile *d_t = nullptr;
     int *d_n = nullptr;
@@ -363,7 +379,7 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&d_l, sizeof L) == cudaSuccess && cudaMalloc(&d_t, sizeof(Tile) * nt) == cudaSuccess &&
         cudaMalloc(&d_n, sizeof(int)) == cudaSuccess && cudaMalloc(&d_s, sizeof(int64_t)) == cudaSuccess &&
-        cudaMalloc(&d_p, sizeof(double) * 9 * nt) == cudaSuccess &&
+        cudaMalloc(&d_p, sizeof(double) * 18 * nt) == cudaSuccess &&
         cudaMalloc(&d_b, sizeof(GridBar)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
         cudaEventCreate(&e1) == cudaSuccess) {
         const int64_t zero = 0;
@@ -380,7 +396,7 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
         const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
                                                       : (const void *)k_batch<float>;
         cudaEventRecord(e0, b->stream);
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, b->stream);
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileThreads), args, 0, b->stream);
         cudaEventRecord(e1, b->stream);
         int err = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &d_b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
@@ -519,7 +535,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     CKB(cudaMalloc(&b->d_ntiles, sizeof(int)));
     CKB(cudaMalloc(&b->d_lat_tiles, sizeof(int2) * n));
     CKB(cudaMalloc(&b->d_steps, sizeof(int64_t) * n));
-    CKB(cudaMalloc(&b->d_tile_part, sizeof(double) * 9 * (size_t)b->max_tiles));
+    CKB(cudaMalloc(&b->d_tile_part, sizeof(double) * 18 * (size_t)b->max_tiles));
     CKB(cudaMalloc(&b->d_bar, sizeof(GridBar)));
     CKB(cudaMalloc(&b->d_U, sizeof(double) * 9 * n));
     CKB(cudaMallocHost(&b->h_steps, sizeof(int64_t) * n));

@@ -39,85 +39,112 @@ __device__ __forceinline__ T inv_norm(int k) {
                    : T(0.125);
 }
 
+// Every add, multiply and fused multiply-add below is an explicitly rounded
+// intrinsic (__fadd_rn, __fmul_rn, __fmaf_rn and their double forms).  The
+// compiler may neither contract these into other FMAs nor reorder them, so
+// every kernel that inlines the collision (single-lattice steps, the batched
+// persistent kernel, the adjoint's state capture) performs the same
+// roundings in the same order and produces the same bits for the same node.
+// Left to itself the compiler fuses a*b + c where it sees fit, and that
+// choice differs between kernels.
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // m = M g.
 template <typename T>
 __device__ __forceinline__ void moments_of(const T g[Q], T m[Q]) {
-    const T sx = g[1] + g[2], dx = g[1] - g[2];
-    const T sy = g[3] + g[4], dy = g[3] - g[4];
-    const T sz = g[5] + g[6], dz = g[5] - g[6];
-    const T s1 = g[7] + g[8], d1 = g[7] - g[8];        // (1, 1, 0)
-    const T s2 = g[9] + g[10], d2 = g[9] - g[10];      // (1,-1, 0)
-    const T s3 = g[11] + g[12], d3 = g[11] - g[12];    // (1, 0, 1)
-    const T s4 = g[13] + g[14], d4 = g[13] - g[14];    // (1, 0,-1)
-    const T s5 = g[15] + g[16], d5 = g[15] - g[16];    // (0, 1, 1)
-    const T s6 = g[17] + g[18], d6 = g[17] - g[18];    // (0, 1,-1)
-    const T sa = sx + sy + sz;
-    const T sxy = s1 + s2, sxz = s3 + s4, syz = s5 + s6;
-    const T se = sxy + sxz + syz;
-    m[0] = g[0] + sa + se;
-    m[1] = T(-30) * g[0] - T(11) * sa + T(8) * se;
-    m[2] = T(12) * g[0] - T(4) * sa + se;
-    const T ex = d1 + d2 + d3 + d4;  // edge part of the x-odd moments
-    const T ey = d1 - d2 + d5 + d6;
-    const T ez = d3 - d4 + d5 - d6;
-    m[3] = dx + ex;
-    m[4] = T(-4) * dx + ex;
-    m[5] = dy + ey;
-    m[6] = T(-4) * dy + ey;
-    m[7] = dz + ez;
-    m[8] = T(-4) * dz + ez;
-    m[9] = T(2) * sx - sy - sz + sxy + sxz - T(2) * syz;
-    m[10] = T(-4) * sx + T(2) * (sy + sz) + sxy + sxz - T(2) * syz;
-    m[11] = sy - sz + sxy - sxz;
-    m[12] = T(2) * (sz - sy) + sxy - sxz;
-    m[13] = s1 - s2;
-    m[14] = s5 - s6;
-    m[15] = s3 - s4;
-    m[16] = d1 + d2 - d3 - d4;
-    m[17] = d5 + d6 - d1 + d2;
-    m[18] = d3 - d4 - d5 + d6;
+    const T sx = radd(g[1], g[2]), dx = rsub(g[1], g[2]);
+    const T sy = radd(g[3], g[4]), dy = rsub(g[3], g[4]);
+    const T sz = radd(g[5], g[6]), dz = rsub(g[5], g[6]);
+    const T s1 = radd(g[7], g[8]), d1 = rsub(g[7], g[8]);        // (1, 1, 0)
+    const T s2 = radd(g[9], g[10]), d2 = rsub(g[9], g[10]);      // (1,-1, 0)
+    const T s3 = radd(g[11], g[12]), d3 = rsub(g[11], g[12]);    // (1, 0, 1)
+    const T s4 = radd(g[13], g[14]), d4 = rsub(g[13], g[14]);    // (1, 0,-1)
+    const T s5 = radd(g[15], g[16]), d5 = rsub(g[15], g[16]);    // (0, 1, 1)
+    const T s6 = radd(g[17], g[18]), d6 = rsub(g[17], g[18]);    // (0, 1,-1)
+    const T syz_ax = radd(sy, sz);
+    const T sa = radd(sx, syz_ax);
+    const T sxy = radd(s1, s2), sxz = radd(s3, s4), syz = radd(s5, s6);
+    const T sxy_xz = radd(sxy, sxz);
+    const T se = radd(sxy_xz, syz);
+    m[0] = radd(radd(g[0], sa), se);
+    m[1] = rfma(T(-30), g[0], rfma(T(-11), sa, rmul(T(8), se)));
+    m[2] = rfma(T(12), g[0], rfma(T(-4), sa, se));
+    const T ex = radd(radd(d1, d2), radd(d3, d4));  // edge part of the x-odd moments
+    const T ey = radd(rsub(d1, d2), radd(d5, d6));
+    const T ez = radd(rsub(d3, d4), rsub(d5, d6));
+    m[3] = radd(dx, ex);
+    m[4] = rfma(T(-4), dx, ex);
+    m[5] = radd(dy, ey);
+    m[6] = rfma(T(-4), dy, ey);
+    m[7] = radd(dz, ez);
+    m[8] = rfma(T(-4), dz, ez);
+    const T e9 = rfma(T(-2), syz, sxy_xz);  // sxy + sxz - 2 syz
+    m[9] = rfma(T(2), sx, rsub(e9, syz_ax));
+    m[10] = rfma(T(-4), sx, rfma(T(2), syz_ax, e9));
+    const T dyz = rsub(sy, sz), dxyz = rsub(sxy, sxz);
+    m[11] = radd(dyz, dxyz);
+    m[12] = rfma(T(-2), dyz, dxyz);
+    m[13] = rsub(s1, s2);
+    m[14] = rsub(s5, s6);
+    m[15] = rsub(s3, s4);
+    m[16] = rsub(radd(d1, d2), radd(d3, d4));
+    m[17] = rsub(radd(d5, d6), rsub(d1, d2));
+    m[18] = rsub(rsub(d3, d4), rsub(d5, d6));
 }
 
 // g = M^T a (so g = M^-1 m for a_k = m_k / D_k).
 template <typename T>
 __device__ __forceinline__ void populations_from(const T a[Q], T g[Q]) {
-    g[0] = a[0] - T(30) * a[1] + T(12) * a[2];
-    const T axis = a[0] - T(11) * a[1] - T(4) * a[2];
-    const T bx = axis + T(2) * a[9] - T(4) * a[10];
-    const T ox = a[3] - T(4) * a[4];
-    g[1] = bx + ox;
-    g[2] = bx - ox;
-    const T by = axis - a[9] + T(2) * a[10] + a[11] - T(2) * a[12];
-    const T oy = a[5] - T(4) * a[6];
-    g[3] = by + oy;
-    g[4] = by - oy;
-    const T bz = axis - a[9] + T(2) * a[10] - a[11] + T(2) * a[12];
-    const T oz = a[7] - T(4) * a[8];
-    g[5] = bz + oz;
-    g[6] = bz - oz;
-    const T edge = a[0] + T(8) * a[1] + a[2];
-    const T ox2 = a[3] + a[4], oy2 = a[5] + a[6], oz2 = a[7] + a[8];
-    const T bxy = edge + a[9] + a[10] + a[11] + a[12];
-    const T t1 = ox2 + oy2 + a[16] - a[17];
-    g[7] = bxy + a[13] + t1;
-    g[8] = bxy + a[13] - t1;
-    const T t2 = ox2 - oy2 + a[16] + a[17];
-    g[9] = bxy - a[13] + t2;
-    g[10] = bxy - a[13] - t2;
-    const T bxz = edge + a[9] + a[10] - a[11] - a[12];
-    const T t3 = ox2 + oz2 - a[16] + a[18];
-    g[11] = bxz + a[15] + t3;
-    g[12] = bxz + a[15] - t3;
-    const T t4 = ox2 - oz2 - a[16] - a[18];
-    g[13] = bxz - a[15] + t4;
-    g[14] = bxz - a[15] - t4;
-    const T byz = edge - T(2) * (a[9] + a[10]);
-    const T t5 = oy2 + oz2 + a[17] - a[18];
-    g[15] = byz + a[14] + t5;
-    g[16] = byz + a[14] - t5;
-    const T t6 = oy2 - oz2 + a[17] + a[18];
-    g[17] = byz - a[14] + t6;
-    g[18] = byz - a[14] - t6;
+    g[0] = rfma(T(12), a[2], rfma(T(-30), a[1], a[0]));
+    const T axis = rfma(T(-4), a[2], rfma(T(-11), a[1], a[0]));
+    const T bx = rfma(T(-4), a[10], rfma(T(2), a[9], axis));
+    const T ox = rfma(T(-4), a[4], a[3]);
+    g[1] = radd(bx, ox);
+    g[2] = rsub(bx, ox);
+    const T byz_ax = rfma(T(2), a[10], rsub(axis, a[9]));  // axis - a9 + 2 a10
+    const T by = rfma(T(-2), a[12], radd(byz_ax, a[11]));
+    const T oy = rfma(T(-4), a[6], a[5]);
+    g[3] = radd(by, oy);
+    g[4] = rsub(by, oy);
+    const T bz = rfma(T(2), a[12], rsub(byz_ax, a[11]));
+    const T oz = rfma(T(-4), a[8], a[7]);
+    g[5] = radd(bz, oz);
+    g[6] = rsub(bz, oz);
+    const T edge = radd(rfma(T(8), a[1], a[0]), a[2]);
+    const T ox2 = radd(a[3], a[4]), oy2 = radd(a[5], a[6]), oz2 = radd(a[7], a[8]);
+    const T a910 = radd(a[9], a[10]), a1112 = radd(a[11], a[12]);
+    const T e910 = radd(edge, a910);
+    const T bxy = radd(e910, a1112);
+    const T pxy = radd(bxy, a[13]), mxy = rsub(bxy, a[13]);
+    const T t1 = radd(radd(ox2, oy2), rsub(a[16], a[17]));
+    g[7] = radd(pxy, t1);
+    g[8] = rsub(pxy, t1);
+    const T t2 = radd(rsub(ox2, oy2), radd(a[16], a[17]));
+    g[9] = radd(mxy, t2);
+    g[10] = rsub(mxy, t2);
+    const T bxz = rsub(e910, a1112);
+    const T pxz = radd(bxz, a[15]), mxz = rsub(bxz, a[15]);
+    const T t3 = radd(radd(ox2, oz2), rsub(a[18], a[16]));
+    g[11] = radd(pxz, t3);
+    g[12] = rsub(pxz, t3);
+    const T t4 = rsub(rsub(ox2, oz2), radd(a[16], a[18]));
+    g[13] = radd(mxz, t4);
+    g[14] = rsub(mxz, t4);
+    const T byz = rfma(T(-2), a910, edge);
+    const T pyz = radd(byz, a[14]), myz = rsub(byz, a[14]);
+    const T t5 = radd(radd(oy2, oz2), rsub(a[17], a[18]));
+    g[15] = radd(pyz, t5);
+    g[16] = rsub(pyz, t5);
+    const T t6 = radd(rsub(oy2, oz2), radd(a[17], a[18]));
+    g[17] = radd(myz, t6);
+    g[18] = rsub(myz, t6);
 }
 
 // Relaxation rate of moment k.
@@ -132,51 +159,65 @@ __device__ __forceinline__ T rate_of(int k, const Collide<T> &p) {
                    : p.snu;
 }
 
+// Forcing weight 1 - s_k/2 of moment k (non-conserved moments).
+template <typename T>
+__device__ __forceinline__ T half_of(int k, const Collide<T> &p) {
+    return k == 1 ? p.he
+         : k == 2 ? p.heps
+         : (k == 4 || k == 6 || k == 8) ? p.hq
+         : (k == 10 || k == 12) ? p.hpi
+         : k >= 16 ? p.hm
+                   : p.hnu;
+}
+
 // Equilibrium moments (shifted: rho is the deviation) and forcing moments
 // for shifted momentum j (u = j / rho0, rho0 = 1).
 template <typename T>
 __device__ __forceinline__ void eq_and_force(T rho, T jx, T jy, T jz, const Collide<T> &p,
                                              T meq[Q], T mF[Q]) {
     const T q = p.linear ? T(0) : T(1);
-    const T jj = q * (jx * jx + jy * jy + jz * jz);
-    const T qxx = q * (T(2) * jx * jx - jy * jy - jz * jz);
-    const T qww = q * (jy * jy - jz * jz);
+    const T q2 = p.linear ? T(0) : T(2);
+    const T xx = rmul(jx, jx), yy = rmul(jy, jy), zz = rmul(jz, jz);
+    const T jj = rmul(q, radd(radd(xx, yy), zz));
+    const T qxx = rmul(q, rsub(rsub(rmul(T(2), xx), yy), zz));
+    const T qww = rmul(q, rsub(yy, zz));
     meq[0] = rho;
-    meq[1] = T(-11) * rho + T(19) * jj;
-    meq[2] = T(3) * rho - T(5.5) * jj;
+    meq[1] = rfma(T(19), jj, rmul(T(-11), rho));
+    meq[2] = rfma(T(-5.5), jj, rmul(T(3), rho));
     meq[3] = jx;
-    meq[4] = T(-2.0 / 3.0) * jx;
+    meq[4] = rmul(T(-2.0 / 3.0), jx);
     meq[5] = jy;
-    meq[6] = T(-2.0 / 3.0) * jy;
+    meq[6] = rmul(T(-2.0 / 3.0), jy);
     meq[7] = jz;
-    meq[8] = T(-2.0 / 3.0) * jz;
+    meq[8] = rmul(T(-2.0 / 3.0), jz);
     meq[9] = qxx;
-    meq[10] = T(-0.5) * qxx;
+    meq[10] = rmul(T(-0.5), qxx);
     meq[11] = qww;
-    meq[12] = T(-0.5) * qww;
-    meq[13] = q * jx * jy;
-    meq[14] = q * jy * jz;
-    meq[15] = q * jx * jz;
+    meq[12] = rmul(T(-0.5), qww);
+    meq[13] = rmul(q, rmul(jx, jy));
+    meq[14] = rmul(q, rmul(jy, jz));
+    meq[15] = rmul(q, rmul(jx, jz));
     meq[16] = meq[17] = meq[18] = T(0);
-    const T uF = q * (jx * p.Fx + jy * p.Fy + jz * p.Fz);
-    const T fxx = q * T(2) * (T(2) * jx * p.Fx - jy * p.Fy - jz * p.Fz);
-    const T fww = q * T(2) * (jy * p.Fy - jz * p.Fz);
+    const T xF = rmul(jx, p.Fx), yF = rmul(jy, p.Fy), zF = rmul(jz, p.Fz);
+    const T uF = rmul(q, radd(radd(xF, yF), zF));
+    const T fxx = rmul(q2, rsub(rsub(rmul(T(2), xF), yF), zF));
+    const T fww = rmul(q2, rsub(yF, zF));
     mF[0] = T(0);
-    mF[1] = T(38) * uF;
-    mF[2] = T(-11) * uF;
+    mF[1] = rmul(T(38), uF);
+    mF[2] = rmul(T(-11), uF);
     mF[3] = p.Fx;
-    mF[4] = T(-2.0 / 3.0) * p.Fx;
+    mF[4] = rmul(T(-2.0 / 3.0), p.Fx);
     mF[5] = p.Fy;
-    mF[6] = T(-2.0 / 3.0) * p.Fy;
+    mF[6] = rmul(T(-2.0 / 3.0), p.Fy);
     mF[7] = p.Fz;
-    mF[8] = T(-2.0 / 3.0) * p.Fz;
+    mF[8] = rmul(T(-2.0 / 3.0), p.Fz);
     mF[9] = fxx;
-    mF[10] = T(-0.5) * fxx;
+    mF[10] = rmul(T(-0.5), fxx);
     mF[11] = fww;
-    mF[12] = T(-0.5) * fww;
-    mF[13] = q * (jx * p.Fy + jy * p.Fx);
-    mF[14] = q * (jy * p.Fz + jz * p.Fy);
-    mF[15] = q * (jx * p.Fz + jz * p.Fx);
+    mF[12] = rmul(T(-0.5), fww);
+    mF[13] = rmul(q, rfma(jx, p.Fy, rmul(jy, p.Fx)));
+    mF[14] = rmul(q, rfma(jy, p.Fz, rmul(jz, p.Fy)));
+    mF[15] = rmul(q, rfma(jx, p.Fz, rmul(jz, p.Fx)));
     mF[16] = mF[17] = mF[18] = T(0);
 }
 
@@ -186,16 +227,25 @@ __device__ __forceinline__ void mrt_collide(T g[Q], const Collide<T> &p, T &jx_o
                                             T &jz_out) {
     T m[Q], meq[Q], mF[Q];
     moments_of<T>(g, m);
-    const T jx = m[3] + T(0.5) * p.Fx, jy = m[5] + T(0.5) * p.Fy, jz = m[7] + T(0.5) * p.Fz;
+    const T jx = rfma(T(0.5), p.Fx, m[3]), jy = rfma(T(0.5), p.Fy, m[5]),
+            jz = rfma(T(0.5), p.Fz, m[7]);
     jx_out = jx;
     jy_out = jy;
     jz_out = jz;
     eq_and_force<T>(m[0], jx, jy, jz, p, meq, mF);
-    // m*_k = m_k - s_k (m_k - meq_k) + (1 - s_k/2) mF_k, scaled by 1/D_k
+    // m*_k = m_k - s_k (m_k - meq_k) + (1 - s_k/2) mF_k, scaled by 1/D_k.
+    // The conserved moments (s_k = 0: rho, j) reduce to m_k + mF_k.
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        const T s = rate_of<T>(k, p);
-        m[k] = (m[k] - s * (m[k] - meq[k]) + (T(1) - T(0.5) * s) * mF[k]) * inv_norm<T>(k);
+        T r;
+        if (k == 0 || k == 3 || k == 5 || k == 7) {
+            r = k == 0 ? m[0] : radd(m[k], mF[k]);
+        } else {
+            const T s = rate_of<T>(k, p);
+            r = rfma(-s, rsub(m[k], meq[k]), m[k]);
+            r = rfma(half_of<T>(k, p), mF[k], r);
+        }
+        m[k] = rmul(r, inv_norm<T>(k));
     }
     populations_from<T>(m, g);
 }

@@ -44,9 +44,35 @@ constexpr uint32_t SOLID_BIT = 1u << 31;
 template <typename T>
 struct Collide {
     T se, seps, sq, snu, spi, sm;  // diag(S) of eq. (MRT params), grouped
+    T he, heps, hq, hnu, hpi, hm;  // 1 - s/2 of each group (forcing weight)
     T Fx, Fy, Fz;                  // body force density
     int linear;                    // drop quadratic equilibrium / forcing terms
 };
+
+// Collision parameters in the kernel's arithmetic type from the FP64 rates
+// s[19] (moment order) and force.  Every kernel that steps a lattice takes
+// its parameters from here, so all of them see the same values.
+template <typename T>
+inline Collide<T> make_collide(const double s[19], const double F[3], int linear) {
+    Collide<T> p;
+    p.se = (T)s[1];
+    p.seps = (T)s[2];
+    p.sq = (T)s[4];
+    p.snu = (T)s[9];
+    p.spi = (T)s[10];
+    p.sm = (T)s[16];
+    p.he = (T)(1.0 - 0.5 * s[1]);
+    p.heps = (T)(1.0 - 0.5 * s[2]);
+    p.hq = (T)(1.0 - 0.5 * s[4]);
+    p.hnu = (T)(1.0 - 0.5 * s[9]);
+    p.hpi = (T)(1.0 - 0.5 * s[10]);
+    p.hm = (T)(1.0 - 0.5 * s[16]);
+    p.Fx = (T)F[0];
+    p.Fy = (T)F[1];
+    p.Fz = (T)F[2];
+    p.linear = linear;
+    return p;
+}
 
 struct Dims {
     int Lx, Ly, Lz;
@@ -72,11 +98,12 @@ template <>
 struct Store<__half> {
     using C = float;
     // stored value h = 2^S (f - w); `scale` carries 2^S on store, 2^-S on load
+    // (rounded multiplies: never fused into the arithmetic around them)
     static __device__ __forceinline__ float ld(const __half *p, float inv) {
-        return __half2float(*p) * inv;
+        return __fmul_rn(__half2float(*p), inv);
     }
     static __device__ __forceinline__ void st(__half *p, float v, float sc) {
-        *p = __float2half_rn(v * sc);
+        *p = __float2half_rn(__fmul_rn(v, sc));
     }
 };
 
@@ -113,6 +140,34 @@ __host__ __forceinline__ uint64_t div_magic(uint32_t L) {
 
 __device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t L, uint64_t m) {
     return L == 1 ? n : (uint32_t)__umul64hi((uint64_t)n, m);
+}
+
+// Population access that bypasses L1 (cached in L2 only): needed where one
+// kernel launch reads, in a later step, what other blocks wrote in an
+// earlier one (the persistent batch kernel), since L1 is not coherent
+// across SMs and is only invalidated between launches.
+template <typename S>
+struct StoreL2 {
+    using C = typename Store<S>::C;
+    static __device__ __forceinline__ C ld(const S *p, float s);
+    static __device__ __forceinline__ void st(S *p, C v, float s);
+};
+template <>
+__device__ __forceinline__ double StoreL2<double>::ld(const double *p, float) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ void StoreL2<double>::st(double *p, double v, float) { __stcg(p, v); }
+template <>
+__device__ __forceinline__ float StoreL2<float>::ld(const float *p, float) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ void StoreL2<float>::st(float *p, float v, float) { __stcg(p, v); }
+template <>
+__device__ __forceinline__ float StoreL2<__half>::ld(const __half *p, float inv) {
+    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short *>(p));
+    return __fmul_rn(__half2float(__ushort_as_half(b)), inv);
+}
+template <>
+__device__ __forceinline__ void StoreL2<__half>::st(__half *p, float v, float sc) {
+    __stcg(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(__fmul_rn(v, sc))));
 }
 
 // Per-launch reduction target: per-block partial sums of (ux, uy, uz) in

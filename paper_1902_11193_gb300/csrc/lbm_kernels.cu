@@ -379,17 +379,7 @@ SparseMap sparse_map(const lbm_ctx *c) {
 template <typename S>
 int launch_step_t(lbm_ctx *c, bool reduce) {
     using Cm = typename Store<S>::C;
-    Collide<Cm> p;
-    p.se = (Cm)c->s[1];
-    p.seps = (Cm)c->s[2];
-    p.sq = (Cm)c->s[4];
-    p.snu = (Cm)c->s[9];
-    p.spi = (Cm)c->s[10];
-    p.sm = (Cm)c->s[16];
-    p.Fx = (Cm)c->F[0];
-    p.Fy = (Cm)c->F[1];
-    p.Fz = (Cm)c->F[2];
-    p.linear = c->opt.linear_eq;
+    const Collide<Cm> p = make_collide<Cm>(c->s, c->F, c->opt.linear_eq);
     const int bs = c->opt.block_size;
     const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
     const float sts = c->fp16_scale > 0.f ? c->fp16_scale : 1.0f;
