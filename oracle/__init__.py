@@ -69,6 +69,10 @@ def lib():
         L.ora_collide.argtypes = [dp, dp, dp, C.c_int, dp]
         L.ora_links.argtypes = [u8p, i32p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ora_links.restype = C.c_int64
+        L.ora_flags.argtypes = [u8p, i32p, u8p]
+        L.ora_flags.restype = C.c_int64
+        L.ora_set_bounceback.argtypes = [C.c_void_p, C.c_int]
+        L.ora_set_bounceback.restype = C.c_int
         L.ora_create.argtypes = [u8p, i32p, dp, dp, C.c_int]
         L.ora_create.restype = C.c_void_p
         L.ora_destroy.argtypes = [C.c_void_p]
@@ -184,10 +188,21 @@ def links(mask: np.ndarray):
     return fi[:Nf], nbr[: 18 * Nf].reshape(18, Nf), bb[:Nf], lk
 
 
-class Solver:
-    """Plain FP64 solver on a mask [Lz, Ly, Lx] (1 = solid)."""
+def flags(mask: np.ndarray) -> np.ndarray:
+    """Voxel flags of the image analysis: 0 fluid, 1 bounceback voxel (solid
+    with a fluid link neighbour), 2 other solid; shape of the mask."""
+    mask = np.ascontiguousarray(mask, np.uint8)
+    dims = np.array(mask.shape[::-1], np.int32)
+    out = np.zeros_like(mask)
+    lib().ora_flags(mask, dims, out)
+    return out
 
-    def __init__(self, mask: np.ndarray, s, F, linear: bool = False):
+
+class Solver:
+    """Plain FP64 solver on a mask [Lz, Ly, Lx] (1 = solid).  bounceback
+    "halfway" (default) or "fullway" (the paper's scheme of Sec. 3)."""
+
+    def __init__(self, mask: np.ndarray, s, F, linear: bool = False, bounceback: str = "halfway"):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         self.dims = np.array(self.mask.shape[::-1], np.int32)
         self.N = int(self.mask.size)
@@ -196,6 +211,9 @@ class Solver:
         self._h = lib().ora_create(self.mask, self.dims, self.s, self.F, int(linear))
         if not self._h:
             raise ValueError("oracle create failed")
+        mode = {"halfway": 0, "fullway": 1}[bounceback]
+        if lib().ora_set_bounceback(self._h, mode) != 0:
+            raise ValueError("bad bounceback mode")
 
     def close(self):
         if self._h:

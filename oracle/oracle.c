@@ -262,7 +262,37 @@ struct ora_solver {
     double s[Q], F[3];
     int linear;
     int64_t steps;
+    int fullway;   /* 0 halfway bounceback, 1 full-way bounceback */
+    uint8_t *flag; /* full-way: 0 fluid, 1 bounceback voxel, 2 inner solid */
 };
+
+/* Voxel flags of the paper's image analysis (Sec. 3), read with the mask as
+ * the segmented image: a fluid voxel is flagged 0; a solid voxel with at
+ * least one fluid voxel among its 18 link neighbours (periodic) is a
+ * bounceback voxel, flag 1; any other solid voxel is flag 2. */
+int64_t ora_flags(const uint8_t *mask, const int32_t dims[3], uint8_t *flags) {
+    init_tables();
+    const int Lx = dims[0], Ly = dims[1], Lz = dims[2];
+    int64_t nbb = 0;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                int64_t n = x + (int64_t)Lx * (y + (int64_t)Ly * z);
+                uint8_t f = 0;
+                if (mask[n]) {
+                    f = 2;
+                    for (int i = 1; i < Q; ++i) {
+                        int64_t m = wrapi(x + CV[i][0], Lx) +
+                                    (int64_t)Lx * (wrapi(y + CV[i][1], Ly) +
+                                                   (int64_t)Ly * wrapi(z + CV[i][2], Lz));
+                        if (!mask[m]) f = 1;
+                    }
+                }
+                if (f == 1) ++nbb;
+                flags[n] = f;
+            }
+    return nbb;
+}
 
 ora_solver *ora_create(const uint8_t *mask, const int32_t dims[3], const double s[Q],
                        const double F[3], int linear) {
@@ -286,8 +316,20 @@ ora_solver *ora_create(const uint8_t *mask, const int32_t dims[3], const double 
     return h;
 }
 
+int ora_set_bounceback(ora_solver *h, int mode) {
+    if (!h || (mode != 0 && mode != 1)) return -1;
+    h->fullway = mode;
+    if (mode == 1 && !h->flag) {
+        int32_t dims[3] = {h->Lx, h->Ly, h->Lz};
+        h->flag = (uint8_t *)malloc((size_t)h->N);
+        ora_flags(h->solid, dims, h->flag);
+    }
+    return 0;
+}
+
 void ora_destroy(ora_solver *h) {
     if (!h) return;
+    free(h->flag);
     free(h->solid);
     free(h->f);
     free(h->ftmp);
@@ -304,6 +346,16 @@ static void pull(const ora_solver *h, const double *fs, int x, int y, int z, dou
             zs = wrapi(z - CV[i][2], h->Lz);
         int64_t ns = xs + (int64_t)h->Lx * (ys + (int64_t)h->Ly * zs);
         fl[i] = h->solid[ns] ? fs[OPP[i] * h->N + n] : fs[i * h->N + ns];
+    }
+}
+
+/* Pull stream without bounceback: f_i(x) = f*_i(x - c_i) from every
+ * neighbour (full-way bounceback: the bounceback voxels hold populations). */
+static void pull_all(const ora_solver *h, const double *fs, int x, int y, int z, double fl[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        int xs = wrapi(x - CV[i][0], h->Lx), ys = wrapi(y - CV[i][1], h->Ly),
+            zs = wrapi(z - CV[i][2], h->Lz);
+        fl[i] = fs[i * h->N + xs + (int64_t)h->Lx * (ys + (int64_t)h->Ly * zs)];
     }
 }
 
@@ -325,11 +377,21 @@ static void one_step(ora_solver *h, double U[3]) {
         for (int y = 0; y < h->Ly; ++y)
             for (int x = 0; x < h->Lx; ++x) {
                 int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                if (h->fullway && h->flag[n] == 1) {
+                    /* full-way bounceback: what streamed in goes back out
+                     * along the opposite link in the next step */
+                    pull_all(h, h->f, x, y, z, fl);
+                    for (int i = 0; i < Q; ++i) h->ftmp[i * h->N + n] = fl[OPP[i]];
+                    continue;
+                }
                 if (h->solid[n]) {
                     for (int i = 0; i < Q; ++i) h->ftmp[i * h->N + n] = h->f[i * h->N + n];
                     continue;
                 }
-                pull(h, h->f, x, y, z, fl);
+                if (h->fullway)
+                    pull_all(h, h->f, x, y, z, fl);
+                else
+                    pull(h, h->f, x, y, z, fl);
                 if (plane) {
                     node_velocity(h, fl, u);
                     for (int a = 0; a < 3; ++a) plane[3 * z + a] += u[a];
@@ -367,7 +429,10 @@ void ora_velocity(ora_solver *h, double *u) {
                     for (int a = 0; a < 3; ++a) u[a * h->N + n] = 0.0;
                     continue;
                 }
-                pull(h, h->f, x, y, z, fl);
+                if (h->fullway)
+                    pull_all(h, h->f, x, y, z, fl);
+                else
+                    pull(h, h->f, x, y, z, fl);
                 node_velocity(h, fl, v);
                 for (int a = 0; a < 3; ++a) u[a * h->N + n] = v[a];
             }
@@ -621,7 +686,7 @@ int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, i
     int d = 0;
     for (int a = 1; a < 3; ++a)
         if (fabs(h->F[a]) > fabs(h->F[d])) d = a;
-    if (h->F[d] == 0.0) return -1;
+    if (h->F[d] == 0.0 || h->fullway) return -1;
     double p0[4] = {tau, Lambda, 3.0 / 16.0, 3.0 / 16.0};
     if (set == ORA_SET_D) p0[3] = 3.0 / 8.0;
     if (set == ORA_SET_E) p0[2] = p0[3] = Lambda;

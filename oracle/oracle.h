@@ -76,6 +76,17 @@ int ora_run_to_convergence(ora_solver *h, double tol, int64_t K, int64_t max_ste
  * Ubar_a = (U_a + U_b)/2.  U receives the measure the rule stopped on. */
 int ora_run_to_convergence_rule(ora_solver *h, double tol, int64_t K, int64_t max_steps,
                                 int rule, int64_t *steps, double U[3]);
+/* Voxel flags of the image analysis (Sec. 3): flags[N] = 0 fluid, 1 solid
+ * voxel with a fluid voxel among its 18 link neighbours (bounceback voxel),
+ * 2 other solid.  Returns the number of bounceback voxels. */
+int64_t ora_flags(const uint8_t *mask, const int32_t dims[3], uint8_t *flags);
+/* Bounceback scheme: 0 halfway (default: the wall at the half-link, applied
+ * in the pull), 1 full-way (Sec. 3: bounceback voxels receive the populations
+ * streamed into them and return each along the opposite link in the next
+ * step, without collision or force; fluid voxels stream from every
+ * neighbour).  The adjoint and the field-streaming functions assume halfway
+ * bounceback.  Returns 0, or -1 for a bad mode. */
+int ora_set_bounceback(ora_solver *h, int mode);
 void ora_set_threads(int n);
 int ora_get_threads(void);
 
