@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--large", action="store_true", default=True,
                    help="1024^3 low-porosity sparse leg, FP32 vs FP16 storage")
     p.add_argument("--no-large", dest="large", action="store_false")
+    p.add_argument("--channels", default="lowres", choices=["none", "lowres", "full"],
+                   help="the paper's channel study as one batch: lowres = circular bores "
+                        "D = 32, 64 and the 64^2 resolution series; full adds D = 128 and the "
+                        "triangular bore")
     return p.parse_args()
 
 
@@ -375,6 +379,8 @@ def run_ours(args):
         out["adjoint"] = adjoint_run(args, stream)
     if rank == 0 and args.large:
         out["large"] = large_run(args, stream)
+    if rank == 0 and args.channels != "none":
+        out["channels"] = channels_run(args, stream)
 
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, text = oracle_sample(mask)
@@ -542,6 +548,86 @@ def adjoint_run(args, stream):
                 "Lm_dk_dLm_over_k": g["dLambda_m"] * (3 / 8) / k,
                 "F_dk_dF_over_k": g["dF"][0] * 1e-6 / k})
     S.close()
+    return res
+
+
+CHANNEL_TAUS = (0.6, 0.8, 1.0, 1.15, 1.3, 1.6, 2.0)
+CHANNEL_SETS = (("SRT", 3 / 16), ("A", 3 / 16), ("B", 3 / 16), ("C", 3 / 16), ("D", 3 / 16),
+                ("E", 1 / 64), ("E", 3 / 16), ("E", 3 / 8))
+
+
+def channel_geometries(kind):
+    """Circular bores of diameter D in an L^2 section (porosity 0.196) and the
+    equilateral triangle of side 200 in 256^2, as one-voxel periodic slabs, with
+    the references k = pi R^4 / (8 A) and sqrt(3) l^4 / (320 A)."""
+    from paper_1902_11193_gb300 import geometry
+
+    circles = [(32, 128), (64, 256)] + ([(128, 512)] if kind == "full" else [])
+    out = [(f"circle D={D} in {L}^2", geometry.pipe(D, L), np.pi * (D / 2) ** 4 / (8 * L * L))
+           for D, L in circles]
+    if kind == "full":
+        out.append(("triangle l=200 in 256^2", geometry.triangle(200, 256),
+                    np.sqrt(3) * 200.0**4 / (320 * 256 * 256)))
+    return out
+
+
+def channels_run(args, stream):
+    """The paper's channel study (Secs. 4.1-4.2) in one batch: every geometry
+    x rate set x tau, converged (K = 100, tol 1e-10 on the per-check relative
+    change of U), then k / k_ref per geometry and set: mean over tau and the
+    relative spread (max - min) / mean; plus the resolution series of circular
+    bores D = 16, 24, 36, 48 in a 64^2 section (SRT, Set B, Set E(3/8), tau = 1)."""
+    import torch
+
+    from paper_1902_11193_gb300 import geometry, lbm
+
+    geoms = channel_geometries(args.channels)
+    lats, keys = [], []
+    for gname, m, kref in geoms:
+        for st, lam in CHANNEL_SETS:
+            for tau in CHANNEL_TAUS:
+                lats.append(dict(mask=m, set_=st, tau=tau, Lambda=lam, force=(1e-6, 0.0, 0.0)))
+                keys.append((gname, st, lam, tau, kref))
+    series = []
+    for D in (16, 24, 36, 48):
+        m = geometry.pipe(D, 64)
+        for st, lam in (("SRT", 3 / 16), ("B", 3 / 16), ("E", 3 / 8)):
+            lats.append(dict(mask=m, set_=st, tau=1.0, Lambda=lam, force=(1e-6, 0.0, 0.0)))
+            keys.append((f"series D={D}", st, lam, 1.0, np.pi * (D / 2) ** 4 / (8 * 64 * 64)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = lbm.LBMBatch(lats, precision="fp64", check_interval=100, max_steps=2_000_000, stream=stream)
+    steps, status = B.run(1e-10)
+    k = B.permeability()[:, 0]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    lay, _ = B.config()
+    B.close()
+    fluid = np.array([int((l["mask"] == 0).sum()) for l in lats])
+    res = {"workload": "one-voxel periodic slabs, F = 1e-6 along the bore, fp64 batch, "
+                       "K = 100, tol 1e-10; sets SRT, A, B, C, D, E(1/64, 3/16, 3/8); "
+                       "tau " + ", ".join(str(t) for t in CHANNEL_TAUS),
+           "lattices": len(lats), "converged": int(np.sum(status == 0)),
+           "steps_total": int(steps.sum()), "steps_max": int(steps.max()), "wall_s": t1 - t0,
+           "fluid_MLUPS": float(np.sum(fluid * steps)) / (t1 - t0) / 1e6,
+           "layouts": {"aa": int(np.sum(lay == 1)), "sparse": int(np.sum(lay == 2))},
+           "geometries": {}}
+    i = 0
+    for gname, _, _ in geoms:
+        g = {}
+        for st, lam in CHANNEL_SETS:
+            r = k[i:i + len(CHANNEL_TAUS)] / keys[i][4]
+            st_steps = steps[i:i + len(CHANNEL_TAUS)]
+            g[f"{st}({lam:g})" if st == "E" else st] = {
+                "k_over_kref_mean": float(np.mean(r)), "spread": float(np.ptp(r) / np.mean(r)),
+                "steps_tau_min": int(st_steps[0]), "steps_tau_max": int(st_steps[-1])}
+            i += len(CHANNEL_TAUS)
+        res["geometries"][gname] = g
+    ser = {}
+    for j in range(i, len(lats)):
+        gname, st, lam, _, kref = keys[j]
+        ser.setdefault(gname, {})[f"{st}({lam:g})" if st == "E" else st] = float(k[j] / kref)
+    res["resolution_series_k_over_kref"] = ser
     return res
 
 

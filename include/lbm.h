@@ -85,6 +85,18 @@ typedef struct {
                                  modes of eigenvalue near -1 that keep the per-step
                                  value alternating around the fixed point; the
                                  two-step mean cancels them. */
+    int32_t bounceback;       /* 0 (default): halfway bounceback, the wall at the
+                                 half-link, applied in the pull of each fluid node.
+                                 1: full-way bounceback (Sec. 3): solid voxels with a
+                                 fluid link neighbour (flag 1 of the image analysis)
+                                 hold the populations streamed into them and return
+                                 each along the opposite link in the next step,
+                                 without collision or force.  Same steady state as
+                                 halfway bounceback, one step more per reflection.
+                                 LBM_LAYOUT_AB only (LBM_EINVAL otherwise); its
+                                 bounceback voxels are internal state: velocity 0,
+                                 rest populations in lbm_get_populations, untouched
+                                 by lbm_set_populations; no adjoint (LBM_ENOSTATE). */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;

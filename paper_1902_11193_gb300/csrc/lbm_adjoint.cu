@@ -50,7 +50,7 @@ struct AdjUnit {
             fluid = true;
         } else {
             bits = v.lw[u];
-            fluid = !(bits & SOLID_BIT);
+            fluid = !(bits & NOT_FLUID);
             if (fluid) d.init(u, v.d);
         }
     }

@@ -55,6 +55,7 @@ void lbm_default_options(lbm_options *o) {
     o->fp16_scale_log2 = 0;
     o->block_size = 0;
     o->stop_rule = 0;
+    o->bounceback = 0;
 }
 
 // Table 2 (Sec. 2.3); s_nu = 1/tau in every set.
@@ -149,6 +150,8 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     if (o.max_steps <= 0) o.max_steps = 1000000;
     if (o.fp16_scale_log2 < 0 || o.fp16_scale_log2 > 60) return LBM_EINVAL;
     if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
+    if (o.bounceback != 0 && o.bounceback != 1) return LBM_EINVAL;
+    if (o.bounceback == 1 && o.layout != LBM_LAYOUT_AB) return LBM_EINVAL;
     int64_t Nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         if (mask[n] > 1) return LBM_EINVAL;
@@ -413,7 +416,7 @@ static double dsE_dL(double s, double L) {
 
 int lbm_adjoint(lbm_ctx *c, double tol, int64_t max_iter, lbm_grad *out) {
     if (!c || !out || !(tol >= 0.0) || max_iter < 1) return LBM_EINVAL;
-    if (!c->converged) return LBM_ENOSTATE;
+    if (!c->converged || c->opt.bounceback != 0) return LBM_ENOSTATE;
     int d = 0;
     for (int a = 1; a < 3; ++a)
         if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
@@ -607,7 +610,7 @@ struct CkptHeader {
     int32_t precision, layout, check_interval, linear_eq, fp16_scale_log2, block_size;
     int64_t max_steps;
     int64_t steps;
-    int32_t cur;
+    int32_t bounceback;
     int32_t stop_rule;
 };
 
@@ -638,7 +641,7 @@ int lbm_save(lbm_ctx *c, const char *path) {
     h.block_size = c->opt.block_size;
     h.max_steps = c->opt.max_steps;
     h.steps = c->steps;
-    h.cur = 0;
+    h.bounceback = c->opt.bounceback;
     h.stop_rule = c->opt.stop_rule;
     FILE *fp = fopen(path, "wb");
     if (!fp) return LBM_EIO;
@@ -679,6 +682,7 @@ int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
     o.block_size = h.block_size;
     o.max_steps = h.max_steps;
     o.stop_rule = h.stop_rule;
+    o.bounceback = h.bounceback;
     lbm_ctx *c = nullptr;
     int rc = lbm_create_rates(&c, mask.data(), h.dims, h.s, h.F, &o);
     if (rc != LBM_OK) {

@@ -39,6 +39,11 @@ __host__ __device__ constexpr double weight(int i) {
 // Bit 31 of a dense link word marks a solid voxel; bit i (1..18) marks a
 // bounceback link: the upstream neighbour x - c_i is solid.
 constexpr uint32_t SOLID_BIT = 1u << 31;
+// Bit 30 marks a full-way bounceback voxel: a solid voxel with a fluid link
+// neighbour that reflects what streams into it (full-way mode only; its
+// other bits are 0, and so are the bounceback bits of fluid nodes there).
+constexpr uint32_t BBNODE_BIT = 1u << 30;
+constexpr uint32_t NOT_FLUID = SOLID_BIT | BBNODE_BIT;
 
 // Relaxation rates and drive in the arithmetic type of the kernel.
 template <typename T>

@@ -63,9 +63,9 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
     using C = typename Store<S>::C;
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
-    const bool fluid = !(w & SOLID_BIT);
+    const bool fluid = !(w & NOT_FLUID);
     C jx = C(0), jy = C(0), jz = C(0);
-    if (fluid) {
+    if (fluid || (w & BBNODE_BIT)) {
         DenseNode nd;
         nd.init(n, d);
         C g[Q];
@@ -78,9 +78,16 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
             else
                 g[j] = Store<S>::ld(src + (size_t)j * d.N + nd.up(j), ld_scale);
         }
-        mrt_collide<C>(g, p, jx, jy, jz);
+        if (fluid) {
+            mrt_collide<C>(g, p, jx, jy, jz);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], st_scale);
+            for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], st_scale);
+        } else {
+            // full-way bounceback voxel: each population streamed in leaves
+            // along the opposite link in the next step
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[opp(i)], st_scale);
+        }
     }
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
@@ -232,7 +239,7 @@ __device__ __forceinline__ bool state_unit(const StateView &v, uint32_t u, uint3
         return true;
     }
     w = v.lw[u];
-    if (w & SOLID_BIT) return false;
+    if (w & NOT_FLUID) return false;
     un.d.init(u, v.d);
     return true;
 }
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
         }
     } else {
         w = v.lw[node];
-        fluid = !(w & SOLID_BIT);
+        fluid = !(w & NOT_FLUID);
         if (fluid) nd.d.init(node, v.d);
     }
 #pragma unroll

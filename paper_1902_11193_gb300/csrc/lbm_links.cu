@@ -43,22 +43,33 @@ __device__ __forceinline__ void count_links(uint32_t bits, bool valid,
     }
 }
 
+// Dense link words.  Halfway mode: bounceback bits on fluid nodes, SOLID_BIT
+// on solids.  Full-way mode: no bounceback bits (fluid nodes pull from every
+// neighbour), BBNODE_BIT on solids with a fluid link neighbour, SOLID_BIT on
+// the other solids.  The link counts are those of the mask in both modes.
 __global__ void k_link_words(const uint8_t *__restrict__ mask, int Lx, int Ly, int Lz,
-                             uint32_t N, uint32_t *__restrict__ lw,
+                             uint32_t N, int fullway, uint32_t *__restrict__ lw,
                              unsigned long long *links) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bits = 0;
     bool fluid = false;
     if (n < N) {
+        uint32_t word;
         if (mask[n]) {
-            bits = SOLID_BIT;
+            word = SOLID_BIT;
+            if (fullway) {
+#pragma unroll
+                for (int j = 1; j < Q; ++j)
+                    if (!mask[upstream(n, j, Lx, Ly, Lz)]) word = BBNODE_BIT;
+            }
         } else {
             fluid = true;
 #pragma unroll
             for (int j = 1; j < Q; ++j)
                 if (mask[upstream(n, j, Lx, Ly, Lz)]) bits |= 1u << j;
+            word = fullway ? 0u : bits;
         }
-        lw[n] = bits;
+        lw[n] = word;
     }
     count_links(bits, fluid, links);
 }
@@ -193,7 +204,7 @@ __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, in
 int build_dense_links(lbm_ctx *c, unsigned long long *d_links) {
     const uint32_t N = (uint32_t)c->N;
     k_link_words<<<(N + 255) / 256, 256, 0, c->stream>>>(c->d_mask, c->Lx, c->Ly, c->Lz, N,
-                                                          c->d_lw, d_links);
+                                                          c->opt.bounceback, c->d_lw, d_links);
     c->launches++;
     return launch_error(cudaGetLastError());
 }

@@ -62,7 +62,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("check_interval", C.c_int32),
                 ("linear_eq", C.c_int32), ("max_steps", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32),
-                ("stop_rule", C.c_int32)]
+                ("stop_rule", C.c_int32), ("bounceback", C.c_int32)]
 
 
 _lib = None
@@ -151,12 +151,14 @@ class LBMSolver:
     mask: uint8 [Lz, Ly, Lx], 1 = solid.  Either (set_, tau, Lambda) or
     explicit rates s[19].  stream: a cudaStream_t handle (int) or a
     torch.cuda.Stream; None lets the library create its own stream.
+    bounceback: "halfway" (default) or "fullway" (the paper's scheme; AB
+    layout only).
     """
 
     def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
                  rates_=None, precision="fp32", layout="aa", check_interval=100,
                  linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
-                 block_size=0, stop_rule=0):
+                 block_size=0, stop_rule=0, bounceback="halfway"):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         if self.mask.ndim != 3:
             raise ValueError("mask must be [Lz, Ly, Lx]")
@@ -172,6 +174,8 @@ class LBMSolver:
         o.fp16_scale_log2 = int(fp16_scale_log2)
         o.block_size = int(block_size)
         o.stop_rule = int(stop_rule)
+        o.bounceback = {"halfway": 0, "fullway": 1}[bounceback] if isinstance(bounceback, str) \
+            else int(bounceback)
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self.options = o
