@@ -73,6 +73,8 @@ def lib():
         L.ora_flags.restype = C.c_int64
         L.ora_set_bounceback.argtypes = [C.c_void_p, C.c_int]
         L.ora_set_bounceback.restype = C.c_int
+        L.ora_set_domain.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]
+        L.ora_set_domain.restype = C.c_int
         L.ora_create.argtypes = [u8p, i32p, dp, dp, C.c_int]
         L.ora_create.restype = C.c_void_p
         L.ora_destroy.argtypes = [C.c_void_p]
@@ -214,6 +216,14 @@ class Solver:
         mode = {"halfway": 0, "fullway": 1}[bounceback]
         if lib().ora_set_bounceback(self._h, mode) != 0:
             raise ValueError("bad bounceback mode")
+
+    def set_domain(self, pressure_x=False, rho_in=1.0, rho_out=1.0, symmetry_y=False,
+                   symmetry_z=False):
+        """Bounded domain: Zou-He density faces in x, symmetry planes in y and/or z."""
+        sym = (1 if symmetry_y else 0) | (2 if symmetry_z else 0)
+        if lib().ora_set_domain(self._h, int(bool(pressure_x)), float(rho_in), float(rho_out),
+                                sym) != 0:
+            raise ValueError("invalid domain settings")
 
     def close(self):
         if self._h:

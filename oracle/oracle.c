@@ -264,6 +264,9 @@ struct ora_solver {
     int64_t steps;
     int fullway;   /* 0 halfway bounceback, 1 full-way bounceback */
     uint8_t *flag; /* full-way: 0 fluid, 1 bounceback voxel, 2 inner solid */
+    int pressure_x;       /* x faces: Zou-He density boundaries instead of periodic */
+    int symmetry;         /* bit 0: y faces, bit 1: z faces are symmetry (mirror) planes */
+    double rho_in, rho_out;
 };
 
 /* Voxel flags of the paper's image analysis (Sec. 3), read with the mask as
@@ -318,6 +321,7 @@ ora_solver *ora_create(const uint8_t *mask, const int32_t dims[3], const double 
 
 int ora_set_bounceback(ora_solver *h, int mode) {
     if (!h || (mode != 0 && mode != 1)) return -1;
+    if (mode == 1 && (h->pressure_x || h->symmetry)) return -1;
     h->fullway = mode;
     if (mode == 1 && !h->flag) {
         int32_t dims[3] = {h->Lx, h->Ly, h->Lz};
@@ -359,6 +363,85 @@ static void pull_all(const ora_solver *h, const double *fs, int x, int y, int z,
     }
 }
 
+/* Direction with the y (axis 1) or z (axis 2) component of c_i reversed. */
+static int mirror_dir(int i, int axis) {
+    int c[3] = {CV[i][0], CV[i][1], CV[i][2]};
+    c[axis] = -c[axis];
+    for (int j = 0; j < Q; ++j)
+        if (CV[j][0] == c[0] && CV[j][1] == c[1] && CV[j][2] == c[2]) return j;
+    return -1;
+}
+
+/* Pull stream on a bounded domain (Sec. 2.4).
+ * - y and/or z faces as symmetry planes (half a link outside the outer nodes):
+ *   a population whose source lies outside is the specular image of the one
+ *   that left the node next to it along the mirrored direction, so the
+ *   source keeps the node's y (or z) and the direction's y (or z) component
+ *   is reversed;
+ * - x faces with prescribed density (Zou-He): populations entering through
+ *   the face are unknown after streaming and are set by non-equilibrium
+ *   bounceback, f_i = f_opp(i) + 6 w_i c_ix j_x - c_iy N_y - c_iz N_z, with
+ *   j_x from the prescribed density and the known populations, and N_t half
+ *   the tangential momentum of the in-plane populations, so that the node
+ *   carries the prescribed density and no tangential momentum;
+ * - halfway bounceback where the (mirrored) source voxel is solid. */
+static void pull_bounded(const ora_solver *h, const double *fs, int x, int y, int z, double fl[Q]) {
+    const int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+    int unknown[Q] = {0}, any = 0;
+    for (int i = 0; i < Q; ++i) {
+        int xs = x - CV[i][0], ys = y - CV[i][1], zs = z - CV[i][2], dir = i;
+        if (h->pressure_x && (xs < 0 || xs >= h->Lx)) {
+            unknown[i] = any = 1;
+            continue;
+        }
+        xs = wrapi(xs, h->Lx);
+        if ((h->symmetry & 1) && (ys < 0 || ys >= h->Ly)) {
+            ys = y;
+            dir = mirror_dir(dir, 1);
+        } else {
+            ys = wrapi(ys, h->Ly);
+        }
+        if ((h->symmetry & 2) && (zs < 0 || zs >= h->Lz)) {
+            zs = z;
+            dir = mirror_dir(dir, 2);
+        } else {
+            zs = wrapi(zs, h->Lz);
+        }
+        int64_t ns = xs + (int64_t)h->Lx * (ys + (int64_t)h->Ly * zs);
+        fl[i] = h->solid[ns] ? fs[OPP[i] * h->N + n] : fs[dir * h->N + ns];
+    }
+    if (!any) return;
+    const int nx = (x == 0) ? 1 : -1; /* inward normal of the face */
+    const double rho = (x == 0) ? h->rho_in : h->rho_out;
+    double s0 = 0.0, sout = 0.0, Ny = 0.0, Nz = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        if (CV[i][0] == 0) {
+            s0 += fl[i];
+            Ny += 0.5 * CV[i][1] * fl[i];
+            Nz += 0.5 * CV[i][2] * fl[i];
+        } else if (CV[i][0] == -nx) {
+            sout += fl[i];
+        }
+    }
+    const double jx = nx * (rho - s0 - 2.0 * sout);
+    for (int i = 0; i < Q; ++i)
+        if (unknown[i])
+            fl[i] = fl[OPP[i]] + 6.0 * W[i] * CV[i][0] * jx - CV[i][1] * Ny - CV[i][2] * Nz;
+}
+
+int ora_set_domain(ora_solver *h, int pressure_x, double rho_in, double rho_out,
+                   int symmetry) {
+    if (!h || h->fullway || symmetry < 0 || symmetry > 3) return -1;
+    if (pressure_x && (h->Lx < 2 || h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0 ||
+                       !(rho_in > 0.0) || !(rho_out > 0.0)))
+        return -1;
+    h->pressure_x = pressure_x ? 1 : 0;
+    h->symmetry = symmetry;
+    h->rho_in = rho_in;
+    h->rho_out = rho_out;
+    return 0;
+}
+
 /* Velocity of a streamed node: u = (sum_i c_i f_i + F/2) / rho0. */
 static void node_velocity(const ora_solver *h, const double fl[Q], double u[3]) {
     for (int a = 0; a < 3; ++a) {
@@ -390,6 +473,8 @@ static void one_step(ora_solver *h, double U[3]) {
                 }
                 if (h->fullway)
                     pull_all(h, h->f, x, y, z, fl);
+                else if (h->pressure_x || h->symmetry)
+                    pull_bounded(h, h->f, x, y, z, fl);
                 else
                     pull(h, h->f, x, y, z, fl);
                 if (plane) {
@@ -431,6 +516,8 @@ void ora_velocity(ora_solver *h, double *u) {
                 }
                 if (h->fullway)
                     pull_all(h, h->f, x, y, z, fl);
+                else if (h->pressure_x || h->symmetry)
+                    pull_bounded(h, h->f, x, y, z, fl);
                 else
                     pull(h, h->f, x, y, z, fl);
                 node_velocity(h, fl, v);
@@ -686,7 +773,7 @@ int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, i
     int d = 0;
     for (int a = 1; a < 3; ++a)
         if (fabs(h->F[a]) > fabs(h->F[d])) d = a;
-    if (h->F[d] == 0.0 || h->fullway) return -1;
+    if (h->F[d] == 0.0 || h->fullway || h->pressure_x || h->symmetry) return -1;
     double p0[4] = {tau, Lambda, 3.0 / 16.0, 3.0 / 16.0};
     if (set == ORA_SET_D) p0[3] = 3.0 / 8.0;
     if (set == ORA_SET_E) p0[2] = p0[3] = Lambda;

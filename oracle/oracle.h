@@ -87,6 +87,14 @@ int64_t ora_flags(const uint8_t *mask, const int32_t dims[3], uint8_t *flags);
  * neighbour).  The adjoint and the field-streaming functions assume halfway
  * bounceback.  Returns 0, or -1 for a bad mode. */
 int ora_set_bounceback(ora_solver *h, int mode);
+/* Bounded domain (Sec. 2.4): pressure_x = 1 makes the x faces Zou-He
+ * density boundaries (inlet x = 0 at rho_in, outlet x = Lx-1 at rho_out;
+ * requires F = 0 and Lx >= 2); symmetry bit 0 / bit 1 makes the y / z faces
+ * symmetry (mirror) planes half a link outside the outer nodes.  Unset keeps
+ * a direction periodic.  Halfway bounceback only; the adjoint and the
+ * field-streaming functions assume the periodic domain.  Returns 0 or -1. */
+int ora_set_domain(ora_solver *h, int pressure_x, double rho_in, double rho_out,
+                   int symmetry);
 void ora_set_threads(int n);
 int ora_get_threads(void);
 
