@@ -493,7 +493,7 @@ def sweep_run(args, stream):
                           precision="fp32", layout=["ab", "aa", "sparse"][layout],
                           check_interval=K, max_steps=200000, stream=stream)
         rc, st = S.run_to_convergence(1e-6)
-        ks.append(S.permeability())
+        ks.append(S.converged_permeability())  # k of the measure the rule stopped on
         seq_launches += S.kernel_launches
         seq_steps.append(st)
         S.close()

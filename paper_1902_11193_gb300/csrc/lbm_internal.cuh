@@ -202,7 +202,6 @@ struct lbm_ctx {
     int32_t *d_fidx;      // [Nf] sparse: node index of each fluid node
     uint32_t *d_bb;       // [Nf] sparse: bounceback bits
     uint2 *d_nb;          // [Nf] sparse: {node index, bounceback bits} interleaved
-    int persist_grid;     // resident blocks of the persistent odd-step kernel
     lbm::RowWord *d_rw;   // [Ly*Lz][Wr] sparse: row fluid bits + fluid index base
     int32_t *d_rstart;    // [Ly*Lz + 1] sparse: fluid index of each row's first node
     int Wr;               // 32-voxel words per row

@@ -133,39 +133,33 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
-// Persistent odd step of the sparse layout: a grid of resident blocks walks
-// the fluid nodes k, k + stride, ...; each thread loads the next node's
-// {node index, bounceback bits} before it gathers the current node, so that
-// dependent fetch overlaps the previous node's gathers and collision instead
-// of sitting at the head of every node's latency chain.  Steps that measure
-// the mean velocity use the one-node-per-thread kernel above.
-#ifndef LBM_SPARSE_PERSISTENT
-#define LBM_SPARSE_PERSISTENT 1
+// Odd steps without a velocity reduction: NPT nodes per thread.  A block
+// takes a tile of 256 * NPT consecutive fluid nodes and thread t the nodes
+// first + t, first + t + 256, ...; each node's {node index, bounceback bits}
+// record is loaded one node ahead, so that dependent fetch overlaps the
+// previous node's gathers and collision.  Steps that measure the mean
+// velocity use the one-node-per-thread kernel above.  (A persistent
+// grid-stride version of the same loop hides the index chain as well but
+// streams about a fifth slower; four nodes per thread measured best.)
+#ifndef LBM_SPARSE_ODD_NPT
+#define LBM_SPARSE_ODD_NPT 4
 #endif
 
-template <typename S, typename Idx>
+template <typename S, typename Idx, int NPT>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCKS)
-    k_sparse_odd_p(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
+    k_sparse_odd_t(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
                    float ld_scale, float st_scale) {
     using C = typename Store<S>::C;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t k = blockIdx.x * (256u * NPT) + threadIdx.x;
     uint2 nxt = k < Nf ? __ldg(m.nb + k) : make_uint2(0u, 0u);
-    for (; k < Nf; k += stride) {
+#pragma unroll 1
+    for (int r = 0; r < NPT; ++r, k += 256u) {
+        if (k >= Nf) break;
         const uint2 cur = nxt;
-        if (k + stride < Nf) nxt = __ldg(m.nb + k + stride);
+        if (r + 1 < NPT && k + 256u < Nf) nxt = __ldg(m.nb + k + 256u);
         C jx, jy, jz;
         aa_sparse_update<S, true, Idx>(A, m, Nf, k, cur, p, ld_scale, st_scale, jx, jy, jz);
     }
-}
-
-template <typename S, typename Idx>
-int persistent_grid_t() {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_p<S, Idx>, 256, 0);
-    return sms * (per > 0 ? per : 1);
 }
 
 // ------------------------------------------------------- reduction finalise
@@ -411,19 +405,16 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
     default:
         grid = nblocks(c->Nf, bs);
         if (grid == 0) break;
-        if (LBM_SPARSE_PERSISTENT && odd && !reduce) {
-            const bool narrow = 19 * (uint64_t)c->Nf < (uint64_t(1) << 32);
-            if (c->persist_grid == 0)
-                c->persist_grid = narrow ? persistent_grid_t<S, uint32_t>() : persistent_grid_t<S, size_t>();
-            unsigned pg = (unsigned)c->persist_grid;
-            if (pg > grid) pg = grid;
-            if (narrow)
-                k_sparse_odd_p<S, uint32_t><<<pg, 256, 0, c->stream>>>(
+        if (odd && !reduce) {
+            const unsigned tg = (unsigned)((c->Nf + 256 * LBM_SPARSE_ODD_NPT - 1) /
+                                           (256 * LBM_SPARSE_ODD_NPT));
+            if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32))
+                k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT><<<tg, 256, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
             else
-                k_sparse_odd_p<S, size_t><<<pg, 256, 0, c->stream>>>(
+                k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT><<<tg, 256, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
-            grid = pg;
+            grid = tg;
         } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
             if (odd)
                 k_sparse<S, true, uint32_t><<<grid, bs, 0, c->stream>>>(
