@@ -97,6 +97,19 @@ typedef struct {
                                  bounceback voxels are internal state: velocity 0,
                                  rest populations in lbm_get_populations, untouched
                                  by lbm_set_populations; no adjoint (LBM_ENOSTATE). */
+    int32_t pressure_x;       /* 1: the x faces are density boundaries (Zou-He, Sec. 2.4):
+                                 inlet x = 0 at rho_in, outlet x = Lx-1 at rho_out;
+                                 needs force = 0 and Lx >= 2.  k along x then takes
+                                 the pressure gradient c_s^2 (rho_in - rho_out)/(Lx - 1)
+                                 in place of F_x (eq. perm_calc with grad p); k_y, k_z
+                                 are NaN.  0 (default): periodic in x. */
+    int32_t symmetry;         /* bit 0: the y faces, bit 1: the z faces are symmetry
+                                 (mirror) planes half a link outside the outer nodes
+                                 (Sec. 2.4); unset bits stay periodic.  Default 0.
+                                 pressure_x and symmetry need LBM_LAYOUT_AB and
+                                 halfway bounceback; link counts stay those of the
+                                 periodic image; no adjoint (LBM_ENOSTATE). */
+    double rho_in, rho_out;   /* prescribed densities (rho0 = 1), default 1 */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -14,6 +14,8 @@
 namespace lbm {
 int launch_step(lbm_ctx *c, bool reduce);
 int launch_velocity(lbm_ctx *c, double *u_dev, bool reduce);
+int launch_step_bounded(lbm_ctx *c, bool reduce);
+int launch_velocity_bounded(lbm_ctx *c, double *u_dev, bool reduce);
 void launch_export(lbm_ctx *c, double *f_dev);
 void launch_import(lbm_ctx *c, const double *f_dev);
 void launch_export_at(lbm_ctx *c, const int64_t *nodes_dev, int count, double *f_dev);
@@ -56,6 +58,10 @@ void lbm_default_options(lbm_options *o) {
     o->block_size = 0;
     o->stop_rule = 0;
     o->bounceback = 0;
+    o->pressure_x = 0;
+    o->symmetry = 0;
+    o->rho_in = 1.0;
+    o->rho_out = 1.0;
 }
 
 // Table 2 (Sec. 2.3); s_nu = 1/tau in every set.
@@ -152,6 +158,14 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
     if (o.bounceback != 0 && o.bounceback != 1) return LBM_EINVAL;
     if (o.bounceback == 1 && o.layout != LBM_LAYOUT_AB) return LBM_EINVAL;
+    if ((o.pressure_x != 0 && o.pressure_x != 1) || o.symmetry < 0 || o.symmetry > 3)
+        return LBM_EINVAL;
+    if ((o.pressure_x || o.symmetry) && (o.layout != LBM_LAYOUT_AB || o.bounceback != 0))
+        return LBM_EINVAL;
+    if (o.pressure_x && (dims[0] < 2 || force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0 ||
+                         !(o.rho_in > 0.0) || !(o.rho_out > 0.0) || !isfinite(o.rho_in) ||
+                         !isfinite(o.rho_out)))
+        return LBM_EINVAL;
     int64_t Nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         if (mask[n] > 1) return LBM_EINVAL;
@@ -276,17 +290,36 @@ void lbm_destroy(lbm_ctx *c) {
     free_ctx(c);
 }
 
+// Bounded domains (Zou-He faces, mirror planes) step and measure through
+// their own kernels; everything else through the periodic ones.
+static bool bounded(const lbm_ctx *c) { return c->opt.pressure_x || c->opt.symmetry; }
+static int step_launch(lbm_ctx *c, bool reduce) {
+    return bounded(c) ? launch_step_bounded(c, reduce) : launch_step(c, reduce);
+}
+static int velocity_launch(lbm_ctx *c, double *u_dev, bool reduce) {
+    return bounded(c) ? launch_velocity_bounded(c, u_dev, reduce) : launch_velocity(c, u_dev, reduce);
+}
+
+// Drive of eq. (perm_calc) along axis a: the body force, or along x of a
+// pressure-driven domain the pressure gradient c_s^2 (rho_in - rho_out)/(Lx - 1)
+// between the face nodes.
+static double drive_of(const lbm_ctx *c, int a) {
+    if (c->opt.pressure_x)
+        return a == 0 ? (c->opt.rho_in - c->opt.rho_out) / (3.0 * (double)(c->Lx - 1)) : 0.0;
+    return c->F[a];
+}
+
 int lbm_step(lbm_ctx *c, int64_t n) {
     if (!c || n < 0) return LBM_EINVAL;
     if (n > 0) c->converged = c->has_conv = false;
-    for (int64_t t = 0; t < n; ++t) launch_step(c, false);
+    for (int64_t t = 0; t < n; ++t) step_launch(c, false);
     CK(cudaGetLastError());
     return LBM_OK;
 }
 
 // One measuring step: the mean streamed velocity lands in d_U[3*slot..].
 static int measured_step(lbm_ctx *c, int slot) {
-    int nblk = launch_step(c, true);
+    int nblk = step_launch(c, true);
     if (nblk > 0)
         launch_finalize(c, nblk, 1.0 / (double)c->N, c->d_U + 3 * slot);
     else
@@ -307,7 +340,7 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
     if (!c || !(tol >= 0.0)) return LBM_EINVAL;
     int d = 0;
     for (int a = 1; a < 3; ++a)
-        if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
+        if (fabs(drive_of(c, a)) > fabs(drive_of(c, d))) d = a;
     const int rule = c->opt.stop_rule;
     const int64_t K = rule == 1 && c->opt.check_interval < 3 ? 3 : c->opt.check_interval;
     const int64_t maxs = c->opt.max_steps;
@@ -323,12 +356,12 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
         if (rule == 1) {
             // the mean of two consecutive steps, from the chunk's last three
             if (chunk < 3) {
-                for (int64_t t = 0; t < chunk; ++t) launch_step(c, false);
+                for (int64_t t = 0; t < chunk; ++t) step_launch(c, false);
                 CK(cudaGetLastError());
                 done += chunk;
                 break;
             }
-            for (int64_t t = 0; t < chunk - 3; ++t) launch_step(c, false);
+            for (int64_t t = 0; t < chunk - 3; ++t) step_launch(c, false);
             measured_step(c, 0);
             measured_step(c, 1);
             measured_step(c, 2);
@@ -351,7 +384,7 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
             continue;
         }
         if (K >= 2 && chunk >= 2) {
-            for (int64_t t = 0; t < chunk - 2; ++t) launch_step(c, false);
+            for (int64_t t = 0; t < chunk - 2; ++t) step_launch(c, false);
             measured_step(c, 0);
             measured_step(c, 1);
             CK(cudaGetLastError());
@@ -399,7 +432,10 @@ int lbm_converged_permeability(lbm_ctx *c, double k[3]) {
     if (!c || !k) return LBM_EINVAL;
     if (!c->has_conv) return LBM_ENOSTATE;
     const double nu = (c->tau - 0.5) / 3.0;
-    for (int a = 0; a < 3; ++a) k[a] = c->F[a] != 0.0 ? nu * c->U_conv[a] / c->F[a] : NAN;
+    for (int a = 0; a < 3; ++a) {
+        const double g = drive_of(c, a);
+        k[a] = g != 0.0 ? nu * c->U_conv[a] / g : NAN;
+    }
     return LBM_OK;
 }
 
@@ -416,7 +452,7 @@ static double dsE_dL(double s, double L) {
 
 int lbm_adjoint(lbm_ctx *c, double tol, int64_t max_iter, lbm_grad *out) {
     if (!c || !out || !(tol >= 0.0) || max_iter < 1) return LBM_EINVAL;
-    if (!c->converged || c->opt.bounceback != 0) return LBM_ENOSTATE;
+    if (!c->converged || c->opt.bounceback != 0 || bounded(c)) return LBM_ENOSTATE;
     int d = 0;
     for (int a = 1; a < 3; ++a)
         if (fabs(c->F[a]) > fabs(c->F[d])) d = a;
@@ -470,7 +506,7 @@ int lbm_adjoint(lbm_ctx *c, double tol, int64_t max_iter, lbm_grad *out) {
 
 int lbm_mean_velocity(lbm_ctx *c, double U[3]) {
     if (!c || !U) return LBM_EINVAL;
-    int nblk = launch_velocity(c, nullptr, true);
+    int nblk = velocity_launch(c, nullptr, true);
     if (nblk > 0)
         launch_finalize(c, nblk, 1.0 / (double)c->N, c->d_U + 3 * 7);
     else
@@ -488,7 +524,10 @@ int lbm_permeability(lbm_ctx *c, double k[3]) {
     int rc = lbm_mean_velocity(c, U);
     if (rc) return rc;
     const double nu = (c->tau - 0.5) / 3.0;  // nu = c_s^2 (tau - 1/2)
-    for (int a = 0; a < 3; ++a) k[a] = c->F[a] != 0.0 ? nu * U[a] / c->F[a] : NAN;
+    for (int a = 0; a < 3; ++a) {
+        const double g = drive_of(c, a);
+        k[a] = g != 0.0 ? nu * U[a] / g : NAN;
+    }
     return LBM_OK;
 }
 
@@ -499,7 +538,7 @@ int lbm_velocity(lbm_ctx *c, double *u) {
     CK(cudaMalloc(&d_u, bytes));
     cudaError_t e = cudaMemsetAsync(d_u, 0, bytes, c->stream);
     if (e == cudaSuccess) {
-        launch_velocity(c, d_u, false);
+        velocity_launch(c, d_u, false);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, d_u, bytes, cudaMemcpyDeviceToHost, c->stream);
@@ -614,6 +653,12 @@ struct CkptHeader {
     int32_t stop_rule;
 };
 
+// Version 2 appends the bounded-domain settings after the header.
+struct CkptDomain {
+    int32_t pressure_x, symmetry;
+    double rho_in, rho_out;
+};
+
 int lbm_save(lbm_ctx *c, const char *path) {
     if (!c || !path) return LBM_EINVAL;
     const int64_t units = c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
@@ -627,7 +672,7 @@ int lbm_save(lbm_ctx *c, const char *path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.dims[0] = c->Lx;
     h.dims[1] = c->Ly;
     h.dims[2] = c->Lz;
@@ -645,7 +690,9 @@ int lbm_save(lbm_ctx *c, const char *path) {
     h.stop_rule = c->opt.stop_rule;
     FILE *fp = fopen(path, "wb");
     if (!fp) return LBM_EIO;
-    bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(c->h_mask, 1, (size_t)c->N, fp) == (size_t)c->N &&
+    CkptDomain dm{c->opt.pressure_x, c->opt.symmetry, c->opt.rho_in, c->opt.rho_out};
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&dm, sizeof dm, 1, fp) == 1 &&
+              fwrite(c->h_mask, 1, (size_t)c->N, fp) == (size_t)c->N &&
               (bytes == 0 || fwrite(buf.data(), 1, bytes, fp) == bytes);
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBM_OK : LBM_EIO;
@@ -657,7 +704,13 @@ int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
     FILE *fp = fopen(path, "rb");
     if (!fp) return LBM_EIO;
     CkptHeader h;
-    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kMagic, 8) != 0 ||
+        (h.version != 1 && h.version != 2)) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    CkptDomain dm{0, 0, 1.0, 1.0};  // version 1: periodic
+    if (h.version == 2 && fread(&dm, sizeof dm, 1, fp) != 1) {
         fclose(fp);
         return LBM_EIO;
     }
@@ -683,6 +736,10 @@ int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
     o.max_steps = h.max_steps;
     o.stop_rule = h.stop_rule;
     o.bounceback = h.bounceback;
+    o.pressure_x = dm.pressure_x;
+    o.symmetry = dm.symmetry;
+    o.rho_in = dm.rho_in;
+    o.rho_out = dm.rho_out;
     lbm_ctx *c = nullptr;
     int rc = lbm_create_rates(&c, mask.data(), h.dims, h.s, h.F, &o);
     if (rc != LBM_OK) {

@@ -131,6 +131,14 @@ def triangle(l: float, Ly: int, Lz: int | None = None, Lx: int = 1) -> np.ndarra
     return m
 
 
+def pad_x(mask: np.ndarray, layers: int = 5) -> np.ndarray:
+    """Fluid layers before and after a sample along x, the flow direction
+    (Sec. 2.4: inlet and outlet padded with 5 fluid-only layers)."""
+    Lz, Ly, _ = mask.shape
+    pad = np.zeros((Lz, Ly, layers), np.uint8)
+    return np.ascontiguousarray(np.concatenate([pad, np.asarray(mask, np.uint8), pad], axis=2))
+
+
 def random_mask(dims, solid_fraction: float, seed: int) -> np.ndarray:
     """Independent random voxels (structure tests on tiny lattices)."""
     Lx, Ly, Lz = (dims, dims, dims) if np.isscalar(dims) else dims

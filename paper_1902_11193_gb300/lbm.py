@@ -62,7 +62,9 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("check_interval", C.c_int32),
                 ("linear_eq", C.c_int32), ("max_steps", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32),
-                ("stop_rule", C.c_int32), ("bounceback", C.c_int32)]
+                ("stop_rule", C.c_int32), ("bounceback", C.c_int32),
+                ("pressure_x", C.c_int32), ("symmetry", C.c_int32),
+                ("rho_in", C.c_double), ("rho_out", C.c_double)]
 
 
 _lib = None
@@ -152,13 +154,15 @@ class LBMSolver:
     explicit rates s[19].  stream: a cudaStream_t handle (int) or a
     torch.cuda.Stream; None lets the library create its own stream.
     bounceback: "halfway" (default) or "fullway" (the paper's scheme; AB
-    layout only).
+    layout only).  pressure: (rho_in, rho_out) makes the x faces Zou-He
+    density boundaries (force must be 0); symmetry: "y", "z" or "yz" makes
+    those faces mirror planes (AB layout, halfway bounceback).
     """
 
     def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
                  rates_=None, precision="fp32", layout="aa", check_interval=100,
                  linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
-                 block_size=0, stop_rule=0, bounceback="halfway"):
+                 block_size=0, stop_rule=0, bounceback="halfway", pressure=None, symmetry=""):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         if self.mask.ndim != 3:
             raise ValueError("mask must be [Lz, Ly, Lx]")
@@ -176,6 +180,10 @@ class LBMSolver:
         o.stop_rule = int(stop_rule)
         o.bounceback = {"halfway": 0, "fullway": 1}[bounceback] if isinstance(bounceback, str) \
             else int(bounceback)
+        if pressure is not None:
+            o.pressure_x = 1
+            o.rho_in, o.rho_out = (float(v) for v in pressure)
+        o.symmetry = (1 if "y" in symmetry else 0) | (2 if "z" in symmetry else 0)
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self.options = o
