@@ -69,6 +69,8 @@ def lib():
         L.ora_collide.argtypes = [dp, dp, dp, C.c_int, dp]
         L.ora_links.argtypes = [u8p, i32p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ora_links.restype = C.c_int64
+        L.ora_trt_collide.argtypes = [dp, C.c_double, C.c_double, dp, C.c_int, dp]
+        L.ora_trt_collide.restype = None
         L.ora_flags.argtypes = [u8p, i32p, u8p]
         L.ora_flags.restype = C.c_int64
         L.ora_set_bounceback.argtypes = [C.c_void_p, C.c_int]
@@ -172,6 +174,13 @@ def collide(f, s, F, linear: bool = False) -> np.ndarray:
     out = np.zeros(19)
     lib().ora_collide(np.ascontiguousarray(f, np.float64), np.ascontiguousarray(s, np.float64),
                       np.ascontiguousarray(F, np.float64), int(linear), out)
+    return out
+
+
+def trt_collide(f, s_plus, s_minus, F, linear: bool = False) -> np.ndarray:
+    out = np.zeros(19)
+    lib().ora_trt_collide(np.ascontiguousarray(f, np.float64), float(s_plus), float(s_minus),
+                          np.ascontiguousarray(F, np.float64), int(linear), out)
     return out
 
 

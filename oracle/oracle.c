@@ -214,6 +214,38 @@ void ora_collide(const double f[Q], const double s[Q], const double F[3], int li
     }
 }
 
+/* Two-relaxation-time collision in link form (Sec. 2.2): each population is
+ * split with its opposite into the symmetric half (f_i + f_opp)/2, relaxed
+ * with s_plus, and the antisymmetric half (f_i - f_opp)/2, relaxed with
+ * s_minus, towards the same halves of the second-order equilibrium
+ * w_i [rho + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u] (u = j/rho0, j shifted by F/2);
+ * the Guo populations are split the same way and weighted (1 - s/2). */
+void ora_trt_collide(const double f[Q], double s_plus, double s_minus, const double F[3],
+                     int linear, double fout[Q]) {
+    init_tables();
+    double rho = 0.0, j[3] = {0.5 * F[0], 0.5 * F[1], 0.5 * F[2]};
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) j[a] += CV[i][a] * f[i];
+    }
+    double u[3] = {j[0] / RHO0, j[1] / RHO0, j[2] / RHO0};
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double feq[Q], Fi[Q];
+    for (int i = 0; i < Q; ++i) {
+        double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+        feq[i] = W[i] * (rho + 3.0 * cu + (linear ? 0.0 : 4.5 * cu * cu - 1.5 * uu));
+    }
+    ora_guo_populations(u, F, linear, Fi);
+    for (int i = 0; i < Q; ++i) {
+        int o = OPP[i];
+        double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+        double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+        double Fp = 0.5 * (Fi[i] + Fi[o]), Fm = 0.5 * (Fi[i] - Fi[o]);
+        fout[i] = f[i] - s_plus * (fp - ep) - s_minus * (fm - em) + (1.0 - 0.5 * s_plus) * Fp +
+                  (1.0 - 0.5 * s_minus) * Fm;
+    }
+}
+
 static int wrapi(int v, int L) {
     int r = v % L;
     return r < 0 ? r + L : r;

@@ -42,6 +42,11 @@ void ora_force_moments(const double u[3], const double F[3], int linear, double 
 void ora_collide(const double f[19], const double s[19], const double F[3], int linear,
                  double fout[19]);
 
+/* Two-relaxation-time collision in link form with the even rate s_plus and
+ * the odd rate s_minus (the MRT collision for rates with one even and one odd
+ * value: Sets B, E and SRT). */
+void ora_trt_collide(const double f[19], double s_plus, double s_minus, const double F[3],
+                     int linear, double fout[19]);
 /* Link table of a mask: fluid list, pull neighbours (x - c_i) and bounceback
  * bits.  fluid_idx[Nf], nbr[18][Nf] (entry for direction i at (i-1)*Nf + n,
  * -1 where x - c_i is solid), bbmask[Nf] (bit i set iff x - c_i is solid),

@@ -282,3 +282,29 @@ def test_unit_conversion_worked_example():
 def test_splitmix64_reference_vector(geom):
     want = [int(r[0]) for r in golden("splitmix64_seed1234567.txt")]
     assert [int(v) for v in geom.splitmix64(1234567, 5)] == want
+
+
+@pytest.mark.parametrize("st,tau,lam", [("B", 0.7, 3 / 16), ("B", 1.3, 3 / 16), ("E", 0.9, 3 / 8),
+                                        ("E", 1.6, 1 / 64), ("SRT", 0.8, 3 / 16)])
+@pytest.mark.parametrize("linear", [False, True])
+def test_trt_link_form_equals_mrt(ora, st, tau, lam, linear):
+    """Sets with one even and one odd rate: the link-basis TRT collision is the
+    MRT collision (Sec. 2.2), state by state."""
+    s = ora.rates(st, tau, lam)
+    assert s[1] == s[2] == s[9] == s[10] and s[4] == s[16]
+    rng = np.random.default_rng(7)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    for _ in range(20):
+        f = w * (1 + 0.05 * rng.standard_normal(19))
+        F = 1e-3 * rng.standard_normal(3)
+        want = ora.collide(f, s, F, linear)
+        got = ora.trt_collide(f, s[9], s[4], F, linear)
+        assert np.abs(got - want).max() <= 1e-15
+
+
+def test_trt_link_form_differs_for_mrt_only_sets(ora):
+    """Set D has two odd rates: the single-odd-rate link form cannot express it."""
+    s = ora.rates("D", 1.0)
+    f = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12) * (1 + 0.05 * np.sin(np.arange(19)))
+    got = ora.trt_collide(f, s[9], s[4], [1e-4, 0, 0])
+    assert np.abs(got - ora.collide(f, s, [1e-4, 0, 0])).max() > 1e-6
