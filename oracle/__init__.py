@@ -103,6 +103,9 @@ def lib():
         L.ora_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double,
                                   C.c_int64, C.c_int64, dp, C.POINTER(C.c_int64)]
         L.ora_adjoint.restype = C.c_int
+        L.ora_adjoint_transient.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                            C.c_int64, dp]
+        L.ora_adjoint_transient.restype = C.c_int
         _lib = L
     return _lib
 
@@ -306,6 +309,14 @@ class Solver:
         rc = lib().ora_adjoint(self._h, st, float(tau), float(Lambda), float(tol), int(K),
                                int(max_iter), g, C.byref(it))
         return rc, dict(zip(GRAD_KEYS, g)), int(it.value)
+
+    def adjoint_transient(self, set_, tau: float, Lambda: float = 3.0 / 16.0, n: int = 100):
+        """Gradient of k after n more steps (the solver advances n steps):
+        returns (rc, gradient dict)."""
+        st = SET_NAMES[set_] if isinstance(set_, str) else int(set_)
+        g = np.zeros(7)
+        rc = lib().ora_adjoint_transient(self._h, st, float(tau), float(Lambda), int(n), g)
+        return rc, dict(zip(GRAD_KEYS, g))
 
     def permeability(self, tau: float) -> np.ndarray:
         """eq. (perm_calc) with body forcing: k_j = nu <u_j> / F_j, nu = (tau - 1/2)/3."""

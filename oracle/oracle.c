@@ -799,6 +799,51 @@ static int rates_at(int set, const double p[4], double s[Q]) {
     return ora_rates(set, p[0], p[1], s);
 }
 
+/* Adds to acc[0..6] one node's phi . dC/dtheta at the streamed populations
+ * hn: theta = tau, Lambda (Set E), Lambda_q, Lambda_m (Sets B, D, E) by
+ * central differences of the rates (step 1e-5), and the three force
+ * components (C is quadratic in F, so the central difference is exact). */
+static void node_param_grad(const ora_solver *h, int set, const double p0[4], int d,
+                            const double hn[Q], const double phi[Q], double acc[7]) {
+    double cp[Q], cm[Q], sp[Q], sm[Q];
+    /* parameters 0..3: tau, Lambda, Lq, Lm */
+    const double dp[4] = {1e-5, 1e-5, 1e-5, 1e-5};
+    for (int q = 0; q < 4; ++q) {
+        if (q == 1 && set != ORA_SET_E) continue;
+        if ((q == 2 || q == 3) &&
+            !(set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E))
+            continue;
+        double pp[4], pm[4];
+        for (int r = 0; r < 4; ++r) pp[r] = pm[r] = p0[r];
+        if (q == 1) { /* Set E: Lambda moves both magic parameters */
+            pp[2] += dp[1]; pp[3] += dp[1];
+            pm[2] -= dp[1]; pm[3] -= dp[1];
+        } else {
+            pp[q] += dp[q];
+            pm[q] -= dp[q];
+        }
+        rates_at(set, pp, sp);
+        rates_at(set, pm, sm);
+        ora_collide(hn, sp, h->F, h->linear, cp);
+        ora_collide(hn, sm, h->F, h->linear, cm);
+        double sum = 0.0;
+        for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dp[q]);
+        acc[q] += sum;
+    }
+    /* force components: C is quadratic in F */
+    const double dF = 0.5 * fabs(h->F[d]);
+    for (int a = 0; a < 3; ++a) {
+        double Fp[3] = {h->F[0], h->F[1], h->F[2]}, Fm[3] = {h->F[0], h->F[1], h->F[2]};
+        Fp[a] += dF;
+        Fm[a] -= dF;
+        ora_collide(hn, h->s, Fp, h->linear, cp);
+        ora_collide(hn, h->s, Fm, h->linear, cm);
+        double sum = 0.0;
+        for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dF);
+        acc[4 + a] += sum;
+    }
+}
+
 int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, int64_t K,
                 int64_t max_iter, double grad[7], int64_t *iters) {
     init_tables();
@@ -904,45 +949,10 @@ int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, i
             for (int x = 0; x < h->Lx; ++x) {
                 int64_t n = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
                 if (h->solid[n]) continue;
-                double hn[Q], phi[Q], cp[Q], cm[Q], sp[Q], sm[Q];
+                double hn[Q], phi[Q];
                 for (int i = 0; i < Q; ++i) hn[i] = hs[i * N + n];
                 unstream_node(h, psi, x, y, z, phi);
-                /* parameters 0..3: tau, Lambda, Lq, Lm */
-                const double dp[4] = {1e-5, 1e-5, 1e-5, 1e-5};
-                for (int q = 0; q < 4; ++q) {
-                    if (q == 1 && set != ORA_SET_E) continue;
-                    if ((q == 2 || q == 3) &&
-                        !(set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E))
-                        continue;
-                    double pp[4], pm[4];
-                    for (int r = 0; r < 4; ++r) pp[r] = pm[r] = p0[r];
-                    if (q == 1) { /* Set E: Lambda moves both magic parameters */
-                        pp[2] += dp[1]; pp[3] += dp[1];
-                        pm[2] -= dp[1]; pm[3] -= dp[1];
-                    } else {
-                        pp[q] += dp[q];
-                        pm[q] -= dp[q];
-                    }
-                    rates_at(set, pp, sp);
-                    rates_at(set, pm, sm);
-                    ora_collide(hn, sp, h->F, h->linear, cp);
-                    ora_collide(hn, sm, h->F, h->linear, cm);
-                    double sum = 0.0;
-                    for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dp[q]);
-                    acc[q] += sum;
-                }
-                /* force components: C is quadratic in F */
-                const double dF = 0.5 * fabs(h->F[d]);
-                for (int a = 0; a < 3; ++a) {
-                    double Fp[3] = {h->F[0], h->F[1], h->F[2]}, Fm[3] = {h->F[0], h->F[1], h->F[2]};
-                    Fp[a] += dF;
-                    Fm[a] -= dF;
-                    ora_collide(hn, h->s, Fp, h->linear, cp);
-                    ora_collide(hn, h->s, Fm, h->linear, cm);
-                    double sum = 0.0;
-                    for (int i = 0; i < Q; ++i) sum += phi[i] * (cp[i] - cm[i]) / (2.0 * dF);
-                    acc[4 + a] += sum;
-                }
+                node_param_grad(h, set, p0, d, hn, phi, acc);
             }
     /* explicit dependence of J = nu(tau) U_d(h, F) / F_d on the parameters */
     grad[0] = acc[0] + Ud / (3.0 * h->F[d]);
@@ -961,4 +971,92 @@ int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, i
     free(nxt);
     free(old);
     return rc;
+}
+
+/* Gradient of the permeability after n more steps, J = nu U_d(S f_n) / F_d
+ * with f_t the post-collision state t steps from now: reverse accumulation
+ * through every step.  All n + 1 states are kept (the oracle runs small
+ * lattices).  With h_t = S f_{t-1} the state step t collides,
+ *   psi_{n+1} = dJ/dh,  psi_t = J_C(h_t)^T S^T psi_{t+1},
+ *   dJ/dtheta = explicit + sum_t (S^T psi_{t+1}) . dC/dtheta(h_t). */
+int ora_adjoint_transient(ora_solver *h, int set, double tau, double Lambda, int64_t n,
+                          double grad[7]) {
+    init_tables();
+    int d = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(h->F[a]) > fabs(h->F[d])) d = a;
+    if (n < 1 || h->F[d] == 0.0 || h->fullway || h->pressure_x || h->symmetry) return -1;
+    double p0[4] = {tau, Lambda, 3.0 / 16.0, 3.0 / 16.0};
+    if (set == ORA_SET_D) p0[3] = 3.0 / 8.0;
+    if (set == ORA_SET_E) p0[2] = p0[3] = Lambda;
+    double s0[Q];
+    if (rates_at(set, p0, s0) != 0) return -1;
+    for (int k = 0; k < Q; ++k)
+        if (fabs(s0[k] - h->s[k]) > 1e-14) return -1;
+    const int64_t N = h->N;
+    const size_t field = (size_t)Q * N;
+    double *fs = (double *)malloc(sizeof(double) * field * (size_t)(n + 1));
+    if (!fs) return -1;
+    memcpy(fs, h->f, sizeof(double) * field);
+    for (int64_t t = 1; t <= n; ++t) {
+        ora_step(h, 1, NULL);
+        memcpy(fs + field * (size_t)t, h->f, sizeof(double) * field);
+    }
+    double *hs = (double *)malloc(sizeof(double) * field);
+    double *psi = (double *)calloc(field, sizeof(double));
+    double *nxt = (double *)calloc(field, sizeof(double));
+    const double nu = (tau - 0.5) / 3.0;
+    int64_t Nf = 0;
+    double Ud = 0.0;
+    ora_stream_field(h, fs + field * (size_t)n, hs);
+    for (int64_t m = 0; m < N; ++m) {
+        if (h->solid[m]) continue;
+        ++Nf;
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            psi[i * N + m] = nu * CV[i][d] / (h->F[d] * (double)N);
+            acc += CV[i][d] * hs[i * N + m];
+        }
+        Ud += acc + 0.5 * h->F[d];
+    }
+    Ud /= (double)N;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t t = n; t >= 1; --t) {
+        ora_stream_field(h, fs + field * (size_t)(t - 1), hs); /* h_t */
+        for (int z = 0; z < h->Lz; ++z)
+            for (int y = 0; y < h->Ly; ++y)
+                for (int x = 0; x < h->Lx; ++x) {
+                    int64_t m = x + (int64_t)h->Lx * (y + (int64_t)h->Ly * z);
+                    if (h->solid[m]) {
+                        for (int i = 0; i < Q; ++i) nxt[i * N + m] = 0.0;
+                        continue;
+                    }
+                    double hn[Q], phi[Q], J[Q][Q];
+                    for (int i = 0; i < Q; ++i) hn[i] = hs[i * N + m];
+                    unstream_node(h, psi, x, y, z, phi);
+                    node_param_grad(h, set, p0, d, hn, phi, acc);
+                    collide_jacobian(hn, h->s, h->F, h->linear, J);
+                    for (int c = 0; c < Q; ++c) {
+                        double v = 0.0;
+                        for (int i = 0; i < Q; ++i) v += J[i][c] * phi[i];
+                        nxt[c * N + m] = v;
+                    }
+                }
+        double *tmp = psi;
+        psi = nxt;
+        nxt = tmp;
+    }
+    grad[0] = acc[0] + Ud / (3.0 * h->F[d]);
+    const int magic = set == ORA_SET_B || set == ORA_SET_D || set == ORA_SET_E;
+    grad[1] = set == ORA_SET_E ? acc[1] : (magic ? acc[2] + acc[3] : NAN);
+    grad[2] = magic ? acc[2] : NAN;
+    grad[3] = magic ? acc[3] : NAN;
+    for (int a = 0; a < 3; ++a) grad[4 + a] = acc[4 + a];
+    grad[4 + d] += nu * ((double)Nf / (2.0 * (double)N)) / h->F[d] -
+                   nu * Ud / (h->F[d] * h->F[d]);
+    free(fs);
+    free(hs);
+    free(psi);
+    free(nxt);
+    return 0;
 }

@@ -133,6 +133,11 @@ void ora_adjoint_apply(ora_solver *h, const double *in, double *out);
  * parameters (A, C, SRT).  Returns 0, 1 (not converged) or -1. */
 int ora_adjoint(ora_solver *h, int set, double tau, double Lambda, double tol, int64_t K,
                 int64_t max_iter, double grad[7], int64_t *iters);
+/* Gradient of the permeability after n more steps (the solver advances n
+ * steps): reverse accumulation through every step, all states kept.  grad as
+ * for ora_adjoint.  Returns 0, or -1 for bad input. */
+int ora_adjoint_transient(ora_solver *h, int set, double tau, double Lambda, int64_t n,
+                          double grad[7]);
 
 #ifdef __cplusplus
 }

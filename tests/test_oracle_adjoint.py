@@ -105,3 +105,53 @@ def test_adjoint_step_is_the_transpose(ora, geom):
     LTw = S.adjoint_apply(w)
     lhs, rhs = np.sum(Lv * w * fluid), np.sum(v * LTw)
     assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0)
+
+
+def _k_after(ora, mask, s, F, tau, n):
+    S = ora.Solver(mask, s, F)
+    S.step(n)
+    return (tau - 0.5) / 3 * S.mean_velocity()[0] / F[0]
+
+
+def test_transient_adjoint_matches_central_differences(ora, geom):
+    """The gradient of k after n steps from rest (reverse accumulation through
+    every step) against central differences of the oracle's own k(n)."""
+    mask = geom.sphere_array(8, "bcc", r=2.4)
+    tau, n, F = 0.9, 25, [1e-5, 2e-6, 0.0]
+    S = ora.Solver(mask, ora.rates("D", tau), F)
+    rc, g = S.adjoint_transient("D", tau, n=n)
+    assert rc == 0 and S.steps == n
+    k0 = _k_after(ora, mask, ora.rates("D", tau), F, tau, n)
+    h = 1e-4
+    fd = {
+        "dtau": (_k_after(ora, mask, ora.rates("D", tau + h), F, tau + h, n)
+                 - _k_after(ora, mask, ora.rates("D", tau - h), F, tau - h, n)) / (2 * h),
+        "dLambda_q": (_k_after(ora, mask, ora.rates_magic(tau, 3 / 16 + h, 3 / 8), F, tau, n)
+                      - _k_after(ora, mask, ora.rates_magic(tau, 3 / 16 - h, 3 / 8), F, tau, n)) / (2 * h),
+        "dLambda_m": (_k_after(ora, mask, ora.rates_magic(tau, 3 / 16, 3 / 8 + h), F, tau, n)
+                      - _k_after(ora, mask, ora.rates_magic(tau, 3 / 16, 3 / 8 - h), F, tau, n)) / (2 * h),
+    }
+    dF = 1e-4 * F[0]
+    fd["dFx"] = (_k_after(ora, mask, ora.rates("D", tau), [F[0] + dF, F[1], 0], tau, n)
+                 - _k_after(ora, mask, ora.rates("D", tau), [F[0] - dF, F[1], 0], tau, n)) / (2 * dF)
+    scale = {"dtau": tau, "dLambda_q": 3 / 16, "dLambda_m": 3 / 8, "dFx": F[0]}
+    for key, want in fd.items():
+        assert abs(g[key] - want) * scale[key] <= 1e-7 * abs(k0), key
+
+
+def test_transient_adjoint_tends_to_steady(ora, geom):
+    """Once k(n) has stopped changing, the transient gradient is the steady
+    adjoint's."""
+    mask = geom.sphere_array(6, "bcc", r=1.8)
+    tau, F = 1.4, [1e-5, 0.0, 0.0]
+    A = ora.Solver(mask, ora.rates("B", tau), F)
+    rc, g_tr = A.adjoint_transient("B", tau, n=500)
+    assert rc == 0
+    B = ora.Solver(mask, ora.rates("B", tau), F)
+    rc, _, _ = B.run_to_convergence(1e-15, K=10, max_steps=100000)
+    assert rc == 0
+    rc, g_st, _ = B.adjoint("B", tau, tol=1e-14)
+    assert rc == 0
+    k = A.permeability(tau)[0]
+    for key, sc in (("dtau", tau), ("dLambda", 3 / 16), ("dFx", F[0])):
+        assert abs(g_tr[key] - g_st[key]) * sc <= 1e-8 * abs(k), key
