@@ -221,6 +221,36 @@ def oracle_sample(mask, seconds=12.0, nz=64):
     return mlups, oracle.get_threads(), text
 
 
+def oracle_extra(mask):
+    """The oracle on one thread (two steps of a 512 x 512 x 8 slab of the
+    workload) and, on all host threads, the 32^3 simple-cubic case (r = 12,
+    Set E(3/16), tau = 1, F = 1e-6) run to the paper's stopping rule at
+    tol 1e-9."""
+    import oracle
+
+    from paper_1902_11193_gb300 import geometry
+
+    out = {}
+    oracle.set_threads(1)
+    slab = np.ascontiguousarray(mask[:8])
+    O = oracle.Solver(slab, oracle.rates("B", 1.0), [1e-6, 0.0, 0.0])
+    O.step(1)
+    t0 = time.perf_counter()
+    O.step(2)
+    dt = time.perf_counter() - t0
+    out["single_thread_MLUPS"] = int((slab == 0).sum()) * 2 / dt / 1e6
+    oracle.set_threads(os.cpu_count() or 1)
+    m = geometry.sphere_array(32, "sc", r=12)
+    O = oracle.Solver(m, oracle.rates("E", 1.0, 3 / 16), [1e-6, 0.0, 0.0])
+    t0 = time.perf_counter()
+    rc, steps, _ = O.run_to_convergence(1e-9, K=1, max_steps=100000)
+    dt = time.perf_counter() - t0
+    out["sc32_to_convergence"] = {"steps": steps, "seconds": dt, "threads": oracle.get_threads(),
+                                  "fluid_MLUPS": int((m == 0).sum()) * steps / dt / 1e6,
+                                  "converged": rc == 0}
+    return out
+
+
 def run_reference(args):
     dist, rank, ws, _ = (None, 0, 1, 0)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
@@ -386,6 +416,7 @@ def run_ours(args):
         v, cores, text = oracle_sample(mask)
         out["cpu_baseline"] = {"value": v, "unit": "fluid MLUPS", "cores": cores,
                                "kind": "oracle", "sample": text}
+        out["cpu_baseline"].update(oracle_extra(mask))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -548,6 +579,23 @@ def adjoint_run(args, stream):
                 "Lm_dk_dLm_over_k": g["dLambda_m"] * (3 / 8) / k,
                 "F_dk_dF_over_k": g["dF"][0] * 1e-6 / k})
     S.close()
+    # transient adjoint: the gradient of k after the same number of steps
+    # from rest, by a checkpointed reverse sweep
+    T = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision="fp32", layout="sparse",
+                      stream=stream)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    gt = T.adjoint_transient(steps)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    res["transient"] = {
+        "steps": steps, "wall_s": t4 - t3,
+        # forward sweep, recomputation of every segment, adjoint step: three passes
+        "fluid_MLUPS_per_pass": 3 * nf * steps / (t4 - t3) / 1e6,
+        "k": gt["k"], "tau_dk_dtau_over_k": gt["dtau"] * 1.0 / gt["k"],
+        "Lq_dk_dLq_over_k": gt["dLambda_q"] * (3 / 16) / gt["k"],
+        "Lm_dk_dLm_over_k": gt["dLambda_m"] * (3 / 8) / gt["k"]}
+    T.close()
     return res
 
 

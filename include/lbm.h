@@ -110,6 +110,10 @@ typedef struct {
                                  halfway bounceback; link counts stay those of the
                                  periodic image; no adjoint (LBM_ENOSTATE). */
     double rho_in, rho_out;   /* prescribed densities (rho0 = 1), default 1 */
+    int32_t collision;        /* 0 (default): the link-basis TRT form where the rates
+                                 have one even and one odd value (Sets B, E, SRT;
+                                 the same collision as the MRT, fewer operations),
+                                 the moment-space MRT otherwise.  1: always MRT. */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -253,6 +257,18 @@ typedef struct {
  * LBM_EINVAL if every force component is zero.  Allocates four
  * population-sized work arrays for the duration of the call. */
 int lbm_adjoint(lbm_ctx *ctx, double tol, int64_t max_iter, lbm_grad *out);
+
+/* Transient adjoint: the gradient of k_d after n more steps (the value
+ * lbm_permeability returns once the context has taken them), by reverse
+ * accumulation through the n steps (no counterpart in the paper; the
+ * transient k(n) is what its convergence rule watches).  The context
+ * advances n steps.  The forward states are recomputed from checkpoints of
+ * the population array taken every ceil(sqrt(n)) steps, so the call holds
+ * about 2 sqrt(n) population-sized arrays; LBM_ENOMEM if they do not fit.
+ * Arithmetic as lbm_adjoint; iterations = n, residual = NaN.  Halfway
+ * bounceback on a periodic domain (LBM_ENOSTATE otherwise); LBM_EINVAL for
+ * n < 1 or a zero force. */
+int lbm_adjoint_transient(lbm_ctx *ctx, int64_t n, lbm_grad *out);
 
 /* ------------------------------------------------------------------------
  * Batched sweep: many lattices of uneven sizes stepped together, as in the

@@ -25,6 +25,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -308,7 +310,7 @@ static AdjView make_adj_view(const lbm_ctx *c) {
 
 template <typename T>
 static Collide<T> collide_params(const lbm_ctx *c) {
-    return make_collide<T>(c->s, c->F, c->opt.linear_eq);
+    return make_collide<T>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
 }
 
 int launch_step(lbm_ctx *c, bool reduce);
@@ -412,6 +414,131 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
     if (e == cudaSuccess) e = cudaGetLastError();
     cleanup();
     return launch_error(e);
+}
+
+// Transient adjoint: the gradient of k after n more steps, J = k(h_{n+1}),
+// by reverse accumulation.  h_t is the state step t collides; with
+// phi_{n+1} = dJ/dh and phi_t = J_C(h_t)^T S^T phi_{t+1}, the gradient sums
+// are those of k_adj_grad at (h_t, phi_{t+1}) added over t.  The forward
+// states are not all kept: the raw population array is saved every
+// C = ceil(sqrt(n)) steps; the reverse sweep restores each checkpoint, steps
+// through its segment again capturing h_t, and walks the segment backwards.
+// About 2 sqrt(n) fields of device memory.  sums[9] receives N U_d of
+// h_{n+1}; the context ends n steps on, at the forward sweep's final state.
+template <typename T>
+static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[10]) {
+    const AdjView v = make_adj_view(c);
+    const unsigned grid = (unsigned)((v.units + 255) / 256);
+    for (int a = 0; a < 10; ++a) sums[a] = 0.0;
+    if (grid == 0) {
+        for (int64_t t = 0; t < n; ++t) launch_step(c, false);
+        return launch_error(cudaGetLastError());
+    }
+    const int64_t C = (int64_t)ceil(sqrt((double)n));
+    const int64_t nseg = (n + C - 1) / C;
+    const size_t fieldT = (size_t)Q * v.units;            // elements of one adjoint field
+    const size_t sbytes = c->elem * (size_t)Q * v.units;  // bytes of one population state
+    T *Hbuf = nullptr, *psi = nullptr, *nxt = nullptr;
+    unsigned char *ckpt = nullptr;
+    double *part = nullptr, *dsum = nullptr;
+    cudaError_t e = cudaMalloc(&Hbuf, sizeof(T) * fieldT * (size_t)C);
+    if (e == cudaSuccess) e = cudaMalloc(&ckpt, sbytes * (size_t)(nseg + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&psi, sizeof(T) * fieldT);
+    if (e == cudaSuccess) e = cudaMalloc(&nxt, sizeof(T) * fieldT);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 10 * (size_t)grid);
+    if (e == cudaSuccess) e = cudaMalloc(&dsum, sizeof(double) * 10 * (size_t)(n + 1));
+    auto cleanup = [&]() {
+        cudaFree(Hbuf);
+        cudaFree(ckpt);
+        cudaFree(psi);
+        cudaFree(nxt);
+        cudaFree(part);
+        cudaFree(dsum);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();  // clear the failed allocation
+        return LBM_ENOMEM;
+    }
+    std::vector<int64_t> ck_steps(nseg + 1);
+    std::vector<int> ck_cur(nseg + 1);
+    auto state = [&]() -> void * {
+        return c->opt.layout == LBM_LAYOUT_AB ? c->d_pop[c->cur] : c->d_pop[0];
+    };
+    auto save = [&](int64_t k) {
+        ck_steps[k] = c->steps;
+        ck_cur[k] = c->cur;
+        return cudaMemcpyAsync(ckpt + sbytes * (size_t)k, state(), sbytes, cudaMemcpyDeviceToDevice,
+                               c->stream);
+    };
+    auto restore = [&](int64_t k) {
+        c->steps = ck_steps[k];
+        c->cur = ck_cur[k];
+        return cudaMemcpyAsync(state(), ckpt + sbytes * (size_t)k, sbytes, cudaMemcpyDeviceToDevice,
+                               c->stream);
+    };
+    const Collide<T> p = collide_params<T>(c);
+    // forward sweep with checkpoints
+    for (int64_t sg = 0; sg < nseg && e == cudaSuccess; ++sg) {
+        e = save(sg);
+        const int64_t len = (sg + 1) * C <= n ? C : n - sg * C;
+        for (int64_t t = 0; t < len; ++t) launch_step(c, false);
+    }
+    if (e == cudaSuccess) e = save(nseg);
+    // seed phi_{n+1} = coef c_d at fluid nodes (one adjoint step of a zero
+    // field, with the captured final state as a finite linearisation point),
+    // and N U_d of h_{n+1}
+    if (e == cudaSuccess) {
+        capture<T>(c, v, grid, Hbuf, 0);
+        e = cudaMemsetAsync(nxt, 0, sizeof(T) * fieldT, c->stream);
+    }
+    if (e == cudaSuccess) {
+        k_adj_step<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, psi, v, p, (T)coef, d, nullptr);
+        k_adj_grad<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, nxt, v, p, d, part);
+        k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10 * (size_t)n);
+        c->launches += 3;
+    }
+    // reverse sweep, segment by segment
+    int64_t t_global = n;
+    for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+        e = restore(sg);
+        const int64_t len = (sg + 1) * C <= n ? C : n - sg * C;
+        for (int64_t t = 0; t < len; ++t) {
+            capture<T>(c, v, grid, Hbuf + fieldT * (size_t)t, 0);
+            launch_step(c, false);
+        }
+        for (int64_t t = len - 1; t >= 0; --t) {
+            const T *H = Hbuf + fieldT * (size_t)t;
+            --t_global;
+            k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, part);
+            k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid,
+                                                          dsum + 10 * (size_t)t_global);
+            k_adj_step<T><<<grid, 256, 0, c->stream>>>(H, psi, nxt, v, p, (T)0, d, nullptr);
+            c->launches += 3;
+            T *tmp = psi;
+            psi = nxt;
+            nxt = tmp;
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = restore(nseg);
+    std::vector<double> host(10 * (size_t)(n + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host.data(), dsum, sizeof(double) * host.size(), cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+        for (int64_t t = 0; t < n; ++t)
+            for (int a = 0; a < 9; ++a) sums[a] += host[10 * (size_t)t + a];
+        sums[9] = host[10 * (size_t)n + 9];
+    }
+    cleanup();
+    return launch_error(e);
+}
+
+int transient_sums(lbm_ctx *c, int64_t n, int d, double coef, double sums[10]) {
+    if (c->opt.precision == LBM_FP64) return transient_run<double>(c, n, d, coef, sums);
+    return transient_run<float>(c, n, d, coef, sums);
 }
 
 int adjoint_sums(lbm_ctx *c, double tol, int64_t max_iter, int d, double coef, double sums[10],

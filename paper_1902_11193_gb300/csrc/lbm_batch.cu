@@ -301,8 +301,8 @@ BatchLat make_lat(const lbm_ctx *c, int npt) {
     L.lw = c->d_lw;
     if (c->opt.layout == LBM_LAYOUT_SPARSE) L.sm = sparse_map(c);
     L.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
-    L.pf = make_collide<float>(c->s, c->F, c->opt.linear_eq);
-    L.pd = make_collide<double>(c->s, c->F, c->opt.linear_eq);
+    L.pf = make_collide<float>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
+    L.pd = make_collide<double>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
     L.inv_N = 1.0 / (double)c->N;
     return L;
 }

@@ -250,4 +250,113 @@ __device__ __forceinline__ void mrt_collide(T g[Q], const Collide<T> &p, T &jx_o
     populations_from<T>(m, g);
 }
 
+// Link-basis TRT collision (Sec. 2.2, the TRT model in link form).  For
+// rates with a single even rate s+ (s_e = s_eps = s_nu = s_pi) and a single
+// odd rate s- (s_q = s_m) -- Sets B and E and SRT -- the MRT collision above
+// equals relaxing, for each opposite pair (i, opp(i)), the half sum
+// S = (g_i + g_opp)/2 with s+ and the half difference D = (g_i - g_opp)/2
+// with s- towards the same halves of the second-order equilibrium
+// g_i^eq = w_i [rho + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u] (shifted: rho is the
+// deviation), with the Guo populations F_i = w_i [3 c.F - 3 u.F + 9 (c.u)(c.F)]
+// split the same way and weighted (1 - s/2).  u = j + F/2 is the shifted
+// momentum (rho0 = 1).  The conserved moments come out as in the MRT: the
+// mass of (g - g^eq) and of F_i vanish, and the momentum row gives j + F.
+// No moment transform, so fewer operations per node.
+
+// c_i . (x, y, z) for the first direction i of a pair (odd i: its leading
+// nonzero component is +1), rounded left to right.
+template <typename T>
+__device__ __forceinline__ T cdot_first(int i, T x, T y, T z) {
+    T r = cx(i) != 0 ? x : (cy(i) != 0 ? y : z);
+    if (cx(i) != 0 && cy(i) != 0) r = cy(i) > 0 ? radd(r, y) : rsub(r, y);
+    if ((cx(i) != 0 || cy(i) != 0) && cz(i) != 0) r = cz(i) > 0 ? radd(r, z) : rsub(r, z);
+    return r;
+}
+
+// sum over pairs k of sign(c_{2k+1, a}) d[k] for axis a, rounded in pair order
+template <typename T>
+__device__ __forceinline__ T pair_axis_sum(int a, const T d[9]) {
+    T r = T(0);
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1;
+        const int sg = a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i));
+        if (sg == 0) continue;
+        if (first) {
+            r = sg > 0 ? d[k] : -d[k];
+            first = false;
+        } else {
+            r = sg > 0 ? radd(r, d[k]) : rsub(r, d[k]);
+        }
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void trt_collide(T g[Q], const Collide<T> &p, T &jx_out, T &jy_out,
+                                            T &jz_out) {
+    const T q = p.linear ? T(0) : T(1);
+    const T sp = p.snu, sm = p.sq, hp = p.hnu, hm = p.hq;  // s+, s-, 1 - s+/2, 1 - s-/2
+    T sum[9], dif[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        sum[k] = radd(g[2 * k + 1], g[2 * k + 2]);
+        dif[k] = rsub(g[2 * k + 1], g[2 * k + 2]);
+    }
+    T rho = g[0];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) rho = radd(rho, sum[k]);
+    const T ux = rfma(T(0.5), p.Fx, pair_axis_sum<T>(0, dif));
+    const T uy = rfma(T(0.5), p.Fy, pair_axis_sum<T>(1, dif));
+    const T uz = rfma(T(0.5), p.Fz, pair_axis_sum<T>(2, dif));
+    jx_out = ux;
+    jy_out = uy;
+    jz_out = uz;
+    const T uu = rfma(uz, uz, rfma(uy, uy, rmul(ux, ux)));
+    const T uF = rfma(uz, p.Fz, rfma(uy, p.Fy, rmul(ux, p.Fx)));
+    const T A = rfma(rmul(T(-1.5), q), uu, rho);  // rho - 1.5 q u.u
+    const T B = rmul(rmul(T(-3), q), uF);         // -3 q u.F
+    const T q45 = rmul(T(4.5), q), q9 = rmul(T(9), q);
+    {  // rest population: no antisymmetric half
+        const T w0 = T(1.0 / 3.0);
+        const T r = rfma(-sp, rsub(g[0], rmul(w0, A)), g[0]);
+        g[0] = rfma(hp, rmul(w0, B), r);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1;
+        const T w = T(weight(i));
+        const T cu = cdot_first<T>(i, ux, uy, uz);
+        const T cF = cdot_first<T>(i, p.Fx, p.Fy, p.Fz);
+        const T Seq = rmul(w, rfma(rmul(q45, cu), cu, A));
+        const T Fs = rmul(w, rfma(rmul(q9, cu), cF, B));
+        const T Deq = rmul(T(3.0 * weight(i)), cu);
+        const T Fd = rmul(T(3.0 * weight(i)), cF);
+        const T S = rmul(T(0.5), sum[k]), D = rmul(T(0.5), dif[k]);
+        const T Sn = rfma(hp, Fs, rfma(-sp, rsub(S, Seq), S));
+        const T Dn = rfma(hm, Fd, rfma(-sm, rsub(D, Deq), D));
+        g[i] = radd(Sn, Dn);
+        g[i + 1] = rsub(Sn, Dn);
+    }
+}
+
+// The collision a lattice uses: link-basis TRT where its rates allow it
+// (p.trt), the moment-space MRT otherwise.  K fixes the choice at compile
+// time (kCollideMrt, kCollideTrt): a kernel that carries both forms and
+// branches between them runs a few per cent slower than either alone, so
+// the single-lattice kernels are instantiated per form and the host picks
+// one; kCollideRuntime branches on p.trt (the batched kernel, whose tiles
+// belong to different lattices).
+constexpr int kCollideRuntime = 0, kCollideMrt = 1, kCollideTrt = 2;
+
+template <int K, typename T>
+__device__ __forceinline__ void collide_as(T g[Q], const Collide<T> &p, T &jx_out, T &jy_out,
+                                           T &jz_out) {
+    if (K == kCollideTrt || (K == kCollideRuntime && p.trt))
+        trt_collide<T>(g, p, jx_out, jy_out, jz_out);
+    else
+        mrt_collide<T>(g, p, jx_out, jy_out, jz_out);
+}
+
 }  // namespace lbm

@@ -120,7 +120,7 @@ __device__ __forceinline__ void node_xyz(uint32_t n, const Dims &d, int &x, int 
     y = (int)(t - (uint32_t)z * (uint32_t)d.Ly);
 }
 
-template <typename S>
+template <typename S, int K>
 __global__ void __launch_bounds__(256) k_ab_bounded(const S *__restrict__ src, S *__restrict__ dst,
                                                     const uint8_t *__restrict__ mask, Dims d,
                                                     Domain dom, Collide<typename Store<S>::C> p,
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_ab_bounded(const S *__restrict__ src, S
         node_xyz(n, d, x, y, z);
         C g[Q];
         bounded_pull<S>(src, mask, d, dom, x, y, z, n, lds, g);
-        mrt_collide<C>(g, p, jx, jy, jz);
+        collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], sts);
     }
@@ -184,14 +184,19 @@ static Domain domain_of(const lbm_ctx *c) {
 template <typename S>
 int step_bounded_t(lbm_ctx *c, bool reduce) {
     using C = typename Store<S>::C;
-    const Collide<C> p = make_collide<C>(c->s, c->F, c->opt.linear_eq);
+    const Collide<C> p = make_collide<C>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
     const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
     const float sts = c->fp16_scale > 0.f ? c->fp16_scale : 1.0f;
     const Dims d{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
     const unsigned grid = (unsigned)((c->N + 255) / 256);
-    k_ab_bounded<S><<<grid, 256, 0, c->stream>>>((const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur],
-                                                 c->d_mask, d, domain_of(c), p, lds, sts,
-                                                 reduce ? c->d_partials : nullptr, c->d_flag);
+    if (p.trt)
+        k_ab_bounded<S, kCollideTrt><<<grid, 256, 0, c->stream>>>(
+            (const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur], c->d_mask, d, domain_of(c), p,
+            lds, sts, reduce ? c->d_partials : nullptr, c->d_flag);
+    else
+        k_ab_bounded<S, kCollideMrt><<<grid, 256, 0, c->stream>>>(
+            (const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur], c->d_mask, d, domain_of(c), p,
+            lds, sts, reduce ? c->d_partials : nullptr, c->d_flag);
     c->cur = 1 - c->cur;
     c->launches++;
     c->steps++;

@@ -52,13 +52,15 @@ struct Collide {
     T he, heps, hq, hnu, hpi, hm;  // 1 - s/2 of each group (forcing weight)
     T Fx, Fy, Fz;                  // body force density
     int linear;                    // drop quadratic equilibrium / forcing terms
+    int trt;                       // one even and one odd rate: link-basis collision
 };
 
 // Collision parameters in the kernel's arithmetic type from the FP64 rates
 // s[19] (moment order) and force.  Every kernel that steps a lattice takes
 // its parameters from here, so all of them see the same values.
 template <typename T>
-inline Collide<T> make_collide(const double s[19], const double F[3], int linear) {
+inline Collide<T> make_collide(const double s[19], const double F[3], int linear,
+                               int allow_trt = 1) {
     Collide<T> p;
     p.se = (T)s[1];
     p.seps = (T)s[2];
@@ -76,6 +78,8 @@ inline Collide<T> make_collide(const double s[19], const double F[3], int linear
     p.Fy = (T)F[1];
     p.Fz = (T)F[2];
     p.linear = linear;
+    // s_e = s_eps = s_nu = s_pi and s_q = s_m: the link-basis TRT form applies
+    p.trt = allow_trt && s[1] == s[9] && s[2] == s[9] && s[10] == s[9] && s[16] == s[4];
     return p;
 }
 

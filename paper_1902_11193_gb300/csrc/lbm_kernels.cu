@@ -55,7 +55,7 @@ __device__ __forceinline__ void block_reduce_velocity(C jx, C jy, C jz, bool flu
 
 // ---------------------------------------------------------------- AB pull
 
-template <typename S>
+template <typename S, int K>
 __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__restrict__ dst,
                                             const uint32_t *__restrict__ lw, Dims d,
                                             Collide<typename Store<S>::C> p, float ld_scale,
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
                 g[j] = Store<S>::ld(src + (size_t)j * d.N + nd.up(j), ld_scale);
         }
         if (fluid) {
-            mrt_collide<C>(g, p, jx, jy, jz);
+            collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
             for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], st_scale);
         } else {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
 
 // ------------------------------------------------------ AA, dense and sparse
 
-template <typename S, bool ODD>
+template <typename S, bool ODD, int K>
 __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ lw, Dims d,
                                             Collide<typename Store<S>::C> p, float ld_scale,
                                             float st_scale, Reduce red) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
     C jx = C(0), jy = C(0), jz = C(0);
-    const bool fluid = aa_dense_update<S, ODD>(A, n, w, d, p, ld_scale, st_scale, jx, jy, jz);
+    const bool fluid = aa_dense_update<S, ODD, Store<S>, K>(A, n, w, d, p, ld_scale, st_scale, jx, jy, jz);
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
 #endif
 
 // Idx: type of the flat population offsets; uint32_t whenever 19 * Nf < 2^32.
-template <typename S, bool ODD, typename Idx>
+template <typename S, bool ODD, typename Idx, int K>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
                                        : (ODD ? LBM_SPARSE_MIN_BLOCKS : LBM_SPARSE_MIN_BLOCKS_EVEN))
     k_sparse(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p, float ld_scale,
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     C jx = C(0), jy = C(0), jz = C(0);
     if (fluid) {
         const uint2 nb = ODD ? __ldg(m.nb + k) : make_uint2(0u, 0u);
-        aa_sparse_update<S, ODD, Idx>(A, m, Nf, k, nb, p, ld_scale, st_scale, jx, jy, jz);
+        aa_sparse_update<S, ODD, Idx, Store<S>, K>(A, m, Nf, k, nb, p, ld_scale, st_scale, jx, jy, jz);
     }
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
 #define LBM_SPARSE_ODD_NPT 4
 #endif
 
-template <typename S, typename Idx, int NPT>
+template <typename S, typename Idx, int NPT, int K>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCKS)
     k_sparse_odd_t(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
                    float ld_scale, float st_scale) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCK
         const uint2 cur = nxt;
         if (r + 1 < NPT && k + 256u < Nf) nxt = __ldg(m.nb + k + 256u);
         C jx, jy, jz;
-        aa_sparse_update<S, true, Idx>(A, m, Nf, k, cur, p, ld_scale, st_scale, jx, jy, jz);
+        aa_sparse_update<S, true, Idx, Store<S>, K>(A, m, Nf, k, cur, p, ld_scale, st_scale, jx, jy, jz);
     }
 }
 
@@ -377,10 +377,8 @@ SparseMap sparse_map(const lbm_ctx *c) {
     return m;
 }
 
-template <typename S>
-int launch_step_t(lbm_ctx *c, bool reduce) {
-    using Cm = typename Store<S>::C;
-    const Collide<Cm> p = make_collide<Cm>(c->s, c->F, c->opt.linear_eq);
+template <typename S, int K>
+int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &p) {
     const int bs = c->opt.block_size;
     const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
     const float sts = c->fp16_scale > 0.f ? c->fp16_scale : 1.0f;
@@ -391,16 +389,16 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
     switch (c->opt.layout) {
     case LBM_LAYOUT_AB:
         grid = nblocks(c->N, bs);
-        k_ab<S><<<grid, bs, 0, c->stream>>>((const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur],
+        k_ab<S, K><<<grid, bs, 0, c->stream>>>((const S *)c->d_pop[c->cur], (S *)c->d_pop[1 - c->cur],
                                             c->d_lw, d, p, lds, sts, red);
         c->cur = 1 - c->cur;
         break;
     case LBM_LAYOUT_AA:
         grid = nblocks(c->N, bs);
         if (odd)
-            k_aa<S, true><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
+            k_aa<S, true, K><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
         else
-            k_aa<S, false><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
+            k_aa<S, false, K><<<grid, bs, 0, c->stream>>>((S *)c->d_pop[0], c->d_lw, d, p, lds, sts, red);
         break;
     default:
         grid = nblocks(c->Nf, bs);
@@ -409,25 +407,25 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
             const unsigned tg = (unsigned)((c->Nf + 256 * LBM_SPARSE_ODD_NPT - 1) /
                                            (256 * LBM_SPARSE_ODD_NPT));
             if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32))
-                k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT><<<tg, 256, 0, c->stream>>>(
+                k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT, K><<<tg, 256, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
             else
-                k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT><<<tg, 256, 0, c->stream>>>(
+                k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT, K><<<tg, 256, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
             grid = tg;
         } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
             if (odd)
-                k_sparse<S, true, uint32_t><<<grid, bs, 0, c->stream>>>(
+                k_sparse<S, true, uint32_t, K><<<grid, bs, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
             else
-                k_sparse<S, false, uint32_t><<<grid, bs, 0, c->stream>>>(
+                k_sparse<S, false, uint32_t, K><<<grid, bs, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
         } else {
             if (odd)
-                k_sparse<S, true, size_t><<<grid, bs, 0, c->stream>>>(
+                k_sparse<S, true, size_t, K><<<grid, bs, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
             else
-                k_sparse<S, false, size_t><<<grid, bs, 0, c->stream>>>(
+                k_sparse<S, false, size_t, K><<<grid, bs, 0, c->stream>>>(
                     (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
         }
         break;
@@ -436,6 +434,14 @@ int launch_step_t(lbm_ctx *c, bool reduce) {
     c->steps++;
     if (reduce) return (int)grid;
     return 0;
+}
+
+template <typename S>
+int launch_step_t(lbm_ctx *c, bool reduce) {
+    using Cm = typename Store<S>::C;
+    const Collide<Cm> p = make_collide<Cm>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
+    return p.trt ? launch_step_k<S, kCollideTrt>(c, reduce, p)
+                 : launch_step_k<S, kCollideMrt>(c, reduce, p);
 }
 
 static StateView make_view(const lbm_ctx *c) {

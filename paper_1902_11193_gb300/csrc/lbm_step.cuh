@@ -50,7 +50,7 @@ __device__ __forceinline__ size_t aa_loc_dense(int j, uint32_t n, uint32_t w,
 }
 
 // Dense AA update of node n (link word w); returns false for solid nodes.
-template <typename S, bool ODD, typename Acc = Store<S>>
+template <typename S, bool ODD, typename Acc = Store<S>, int K = kCollideRuntime>
 __device__ __forceinline__ bool aa_dense_update(S *A, uint32_t n, uint32_t w, const Dims &d,
                                                 const Collide<typename Store<S>::C> &p,
                                                 float ld_scale, float st_scale,
@@ -63,7 +63,7 @@ __device__ __forceinline__ bool aa_dense_update(S *A, uint32_t n, uint32_t w, co
     C g[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) g[j] = Acc::ld(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), ld_scale);
-    mrt_collide<C>(g, p, jx, jy, jz);
+    collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
     for (int j = 0; j < Q; ++j)
         Acc::st(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), g[opp(j)], st_scale);
@@ -72,7 +72,7 @@ __device__ __forceinline__ bool aa_dense_update(S *A, uint32_t n, uint32_t w, co
 
 // Sparse AA update of fluid node k; an odd step takes the node's
 // {node index, bounceback bits} as `nb` (already loaded).
-template <typename S, bool ODD, typename Idx, typename Acc = Store<S>>
+template <typename S, bool ODD, typename Idx, typename Acc = Store<S>, int K = kCollideRuntime>
 __device__ __forceinline__ void aa_sparse_update(S *A, const SparseMap &m, uint32_t Nf, uint32_t k,
                                                  uint2 nb, const Collide<typename Store<S>::C> &p,
                                                  float ld_scale, float st_scale,
@@ -95,7 +95,7 @@ __device__ __forceinline__ void aa_sparse_update(S *A, const SparseMap &m, uint3
     C g[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) g[j] = Acc::ld(A + loc[j], ld_scale);
-    mrt_collide<C>(g, p, jx, jy, jz);
+    collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
     for (int j = 0; j < Q; ++j) Acc::st(A + loc[j], g[opp(j)], st_scale);
 }

@@ -64,7 +64,7 @@ class Options(C.Structure):
                 ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32),
                 ("stop_rule", C.c_int32), ("bounceback", C.c_int32),
                 ("pressure_x", C.c_int32), ("symmetry", C.c_int32),
-                ("rho_in", C.c_double), ("rho_out", C.c_double)]
+                ("rho_in", C.c_double), ("rho_out", C.c_double), ("collision", C.c_int32)]
 
 
 _lib = None
@@ -104,6 +104,7 @@ def lib():
             "lbm_save": (C.c_int, [vp, C.c_char_p]),
             "lbm_load": (C.c_int, [C.POINTER(vp), C.c_char_p, C.POINTER(Options)]),
             "lbm_adjoint": (C.c_int, [vp, dbl, i64, C.POINTER(Grad)]),
+            "lbm_adjoint_transient": (C.c_int, [vp, i64, C.POINTER(Grad)]),
             "lbm_mean_velocity_noalloc": (C.c_int, [vp, vp, i32p, dp, vp, vp]),
             "lbm_converged_velocity": (C.c_int, [vp, dp]),
             "lbm_converged_permeability": (C.c_int, [vp, dp]),
@@ -156,13 +157,15 @@ class LBMSolver:
     bounceback: "halfway" (default) or "fullway" (the paper's scheme; AB
     layout only).  pressure: (rho_in, rho_out) makes the x faces Zou-He
     density boundaries (force must be 0); symmetry: "y", "z" or "yz" makes
-    those faces mirror planes (AB layout, halfway bounceback).
+    those faces mirror planes (AB layout, halfway bounceback).  collision:
+    "auto" (link-basis TRT where the rates allow, MRT otherwise) or "mrt".
     """
 
     def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
                  rates_=None, precision="fp32", layout="aa", check_interval=100,
                  linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
-                 block_size=0, stop_rule=0, bounceback="halfway", pressure=None, symmetry=""):
+                 block_size=0, stop_rule=0, bounceback="halfway", pressure=None, symmetry="",
+                 collision="auto"):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         if self.mask.ndim != 3:
             raise ValueError("mask must be [Lz, Ly, Lx]")
@@ -184,6 +187,7 @@ class LBMSolver:
             o.pressure_x = 1
             o.rho_in, o.rho_out = (float(v) for v in pressure)
         o.symmetry = (1 if "y" in symmetry else 0) | (2 if "z" in symmetry else 0)
+        o.collision = {"auto": 0, "mrt": 1}[collision]
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self.options = o
@@ -326,10 +330,21 @@ class LBMSolver:
         """Gradient of the converged permeability along the drive (lbm_adjoint)."""
         g = Grad()
         _check(lib().lbm_adjoint(self._h, float(tol), int(max_iter), C.byref(g)), "lbm_adjoint")
-        return {"dtau": g.dk_dtau, "dLambda": g.dk_dLambda, "dLambda_q": g.dk_dLambda_q,
-                "dLambda_m": g.dk_dLambda_m, "dF": np.array(list(g.dk_dF)),
-                "ds": np.array(list(g.dk_ds)), "k": g.k, "iterations": int(g.iterations),
-                "residual": g.residual}
+        return _grad_dict(g)
+
+    def adjoint_transient(self, n: int) -> dict:
+        """Gradient of the permeability after n more steps
+        (lbm_adjoint_transient); the solver advances n steps."""
+        g = Grad()
+        _check(lib().lbm_adjoint_transient(self._h, int(n), C.byref(g)), "lbm_adjoint_transient")
+        return _grad_dict(g)
+
+
+def _grad_dict(g) -> dict:
+    return {"dtau": g.dk_dtau, "dLambda": g.dk_dLambda, "dLambda_q": g.dk_dLambda_q,
+            "dLambda_m": g.dk_dLambda_m, "dF": np.array(list(g.dk_dF)),
+            "ds": np.array(list(g.dk_ds)), "k": g.k, "iterations": int(g.iterations),
+            "residual": g.residual}
 
 
 class LBMBatch:

@@ -178,3 +178,55 @@ def test_autograd_function(L, geom):
     assert abs(tau.grad.item() - g["dtau"]) <= 1e-9 * abs(g["k"])
     assert abs(lam.grad.item() - g["dLambda"]) <= 1e-9 * abs(g["dLambda"]) + 1e-12
     assert np.allclose(F.grad.numpy(), g["dF"], rtol=1e-9, atol=1e-6)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa", "sparse"])
+@pytest.mark.parametrize("n", [1, 7, 25])
+def test_transient_adjoint_fp64_matches_oracle(L, ora, geom, layout, n):
+    """Checkpointed reverse sweep (segments of ceil(sqrt(n)) steps, the last
+    one shorter for n = 7) against the oracle's store-everything recursion."""
+    mask = geom.sphere_array(8, "bcc", r=2.4)
+    tau, F = 0.9, (1e-5, 2e-6, 0.0)
+    O = ora.Solver(mask, ora.rates("D", tau), list(F))
+    rc, go = O.adjoint_transient("D", tau, n=n)
+    assert rc == 0
+    S = L.LBMSolver(mask, "D", tau, force=F, precision="fp64", layout=layout)
+    g = S.adjoint_transient(n)
+    assert S.steps == n and g["iterations"] == n
+    k = O.permeability(tau)[0]
+    assert abs(g["k"] / k - 1) <= 1e-11
+    # the oracle differences the rates in tau and Lambda with step 1e-5: its
+    # per-step terms carry ~1e-10 relative truncation error
+    for key, sc in (("dtau", tau), ("dLambda_q", 3 / 16), ("dLambda_m", 3 / 8)):
+        assert abs(g[key] - go[key]) * sc <= 1e-8 * abs(k), key
+    for a, key in enumerate(("dFx", "dFy")):
+        assert abs(g["dF"][a] - go[key]) * F[0] <= 1e-9 * abs(k), key
+    # the context ends where a plain n-step run ends
+    P = L.LBMSolver(mask, "D", tau, force=F, precision="fp64", layout=layout)
+    P.step(n)
+    assert np.array_equal(S.velocity(), P.velocity())
+
+
+def test_transient_adjoint_fp32_close_to_fp64(L, geom, boolean48):
+    tau, F, n = 1.0, (1e-6, 0.0, 0.0), 300
+    out = {}
+    for prec in ("fp64", "fp32"):
+        S = L.LBMSolver(boolean48, "B", tau, force=F, precision=prec, layout="sparse")
+        out[prec] = S.adjoint_transient(n)
+    k = out["fp64"]["k"]
+    for key, sc in (("dtau", tau), ("dLambda", 3 / 16)):
+        assert abs(out["fp32"][key] - out["fp64"][key]) * sc <= 1e-4 * abs(k), key
+
+
+def test_transient_adjoint_tends_to_steady(L, geom):
+    mask = geom.sphere_array(10, "bcc", r=3.2)
+    tau, F = 1.4, (1e-6, 0.0, 0.0)
+    A = L.LBMSolver(mask, "B", tau, force=F, precision="fp64", layout="aa", check_interval=10)
+    g_tr = A.adjoint_transient(800)
+    B = L.LBMSolver(mask, "B", tau, force=F, precision="fp64", layout="aa", check_interval=10)
+    rc, _ = B.run_to_convergence(1e-14)
+    assert rc == 0
+    g_st = B.adjoint(1e-13, max_iter=200000)
+    k = g_st["k"]
+    for key, sc in (("dtau", tau), ("dLambda", 3 / 16)):
+        assert abs(g_tr[key] - g_st[key]) * sc <= 1e-8 * abs(k), key

@@ -60,12 +60,14 @@ def test_bounded_fp64_matches_oracle(L, ora, geom, name):
         O.step(n - O.steps)
         S.step(n - S.steps)
         # the oracle carries unshifted populations near 1/3: its roundings are
-        # ~1e-13 of the density and velocity deviations per operation, the
-        # bar of the FP64 stress tests (1e-11 relative, 1e-15 absolute floor)
+        # ~1e-13 of the density and velocity deviations per operation (the
+        # FP64 stress-test bar, 1e-11 relative), and at a Zou-He face it forms
+        # j_x = rho - S_0 - 2 S_out from terms near 1, ~1e-16 absolute per
+        # face node and step; over 60 steps a 5e-15 absolute floor
         uo, ug = O.velocity(), S.velocity()
-        assert np.abs(ug - uo).max() <= 1e-11 * np.abs(uo).max() + 1e-15
+        assert np.abs(ug - uo).max() <= 1e-11 * np.abs(uo).max() + 5e-15
         Uo = O.mean_velocity()
-        assert np.abs(S.mean_velocity() - Uo).max() <= 1e-11 * np.abs(Uo).max() + 1e-15
+        assert np.abs(S.mean_velocity() - Uo).max() <= 1e-11 * np.abs(Uo).max() + 5e-15
     S.close()
 
 
