@@ -165,17 +165,23 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend="nccl"):
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE):
+    (dist, rank, world size, local rank), or (None, 0, 1, 0) alone.  The
+    ranks run independent replicas; the process group carries only the
+    timing barrier and the max-reduce of the timed interval."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
 
         rank = int(os.environ["RANK"])
         local = int(os.environ.get("LOCAL_RANK", rank))
-        import torch
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
         return dist, rank, ws, local
     return None, 0, 1, 0
 
@@ -185,14 +191,20 @@ def barrier(dist):
         dist.barrier()
 
 
-def max_over_ranks(dist, x):
+def max_over_ranks(dist, x, device="cuda"):
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world_size, ms_max):
+    """Whole-job throughput in millions of units per second: every rank's
+    units over the slowest rank's time (weak scaling, fixed work per rank)."""
+    return units_per_rank * steps * world_size / (ms_max * 1e-3) / 1e6
 
 
 # ------------------------------------------------------------------ oracle
@@ -356,7 +368,7 @@ def run_ours(args):
     launches = S.kernel_launches - launches0
     k_fp = S.permeability()
     ms = max_over_ranks(dist, ms)
-    value = nf * args.steps * ws / (ms * 1e-3) / 1e6
+    value = job_throughput(nf, args.steps, ws, ms)
     # the dominant kernel alone: per-launch event timing on its stream
     kmean, kmin = time_kernel_launches(S, 50, stream)
     S.close()
