@@ -230,3 +230,36 @@ def test_transient_adjoint_tends_to_steady(L, geom):
     k = g_st["k"]
     for key, sc in (("dtau", tau), ("dLambda", 3 / 16)):
         assert abs(g_tr[key] - g_st[key]) * sc <= 1e-8 * abs(k), key
+
+
+def test_transient_autograd_matches_differences(L, geom):
+    """transient_permeability's gradients against central differences of GPU
+    FP64 runs of n steps from rest."""
+    import torch
+
+    from paper_1902_11193_gb300.autograd import transient_permeability
+
+    mask = geom.sphere_array(12, "bcc", c=0.3)
+    n, t0, l0, f0 = 60, 0.9, 3 / 8, 1e-5
+    tau = torch.tensor(t0, dtype=torch.float64, requires_grad=True)
+    lam = torch.tensor(l0, dtype=torch.float64, requires_grad=True)
+    F = torch.tensor([f0, 0.0, 0.0], dtype=torch.float64, requires_grad=True)
+    k = transient_permeability(mask, tau, lam, F, n, set_="E", precision="fp64", layout="aa")
+    k.backward()
+
+    def kn(t, lm, fx):
+        S = L.LBMSolver(mask, "E", t, lm, (fx, 0.0, 0.0), precision="fp64", layout="aa")
+        S.step(n)
+        out = S.permeability()[0]
+        S.close()
+        return out
+
+    assert abs(float(k) / kn(t0, l0, f0) - 1) <= 1e-12
+    h = 1e-4
+    fd_tau = (kn(t0 + h, l0, f0) - kn(t0 - h, l0, f0)) / (2 * h)
+    fd_lam = (kn(t0, l0 + h, f0) - kn(t0, l0 - h, f0)) / (2 * h)
+    fd_F = (kn(t0, l0, f0 * (1 + h)) - kn(t0, l0, f0 * (1 - h))) / (2 * h * f0)
+    scale = abs(float(k))
+    assert abs(float(tau.grad) - fd_tau) * t0 <= 1e-6 * scale
+    assert abs(float(lam.grad) - fd_lam) * l0 <= 1e-6 * scale
+    assert abs(float(F.grad[0]) - fd_F) * f0 <= 1e-6 * scale
