@@ -263,3 +263,20 @@ def test_transient_autograd_matches_differences(L, geom):
     assert abs(float(tau.grad) - fd_tau) * t0 <= 1e-6 * scale
     assert abs(float(lam.grad) - fd_lam) * l0 <= 1e-6 * scale
     assert abs(float(F.grad[0]) - fd_F) * f0 <= 1e-6 * scale
+
+
+def test_transient_adjoint_contract(L, geom):
+    mask = geom.sphere_array(10, "bcc", r=3.2)
+    S = L.LBMSolver(mask, "B", 1.0, force=(1e-6, 0, 0), precision="fp64", layout="ab")
+    for n in (0, -3):
+        with pytest.raises(L.LBMError):
+            S.adjoint_transient(n)
+    Z = L.LBMSolver(mask, "B", 1.0, force=(0, 0, 0), precision="fp64", layout="ab")
+    with pytest.raises(L.LBMError):  # no drive, no derivative of k along it
+        Z.adjoint_transient(5)
+    for kw in (dict(bounceback="fullway"), dict(symmetry="y")):
+        X = L.LBMSolver(mask, "B", 1.0, force=(1e-6, 0, 0), precision="fp64", layout="ab", **kw)
+        with pytest.raises(L.LBMError):
+            X.adjoint_transient(5)
+        X.close()
+    assert S.steps == 0  # refused calls leave the context where it was
