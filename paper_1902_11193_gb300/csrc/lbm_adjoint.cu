@@ -119,16 +119,43 @@ __device__ __forceinline__ T dotP(int a, T vx, T vy, T vz, const T w[Q]) {
 
 // phi: the transposed-streamed adjoint at one node; h: the steady streamed
 // populations there.  Returns b = D^-1 M phi and the shifted momentum of h.
+// Shifted momentum j = sum_i c_i h_i + F/2 of a streamed state: the only
+// part of the linearisation point that J_C^T depends on (m^eq and m^F are
+// functions of rho and j, and d m^eq / d rho is constant).
 template <typename T>
-__device__ __forceinline__ void adj_moments(const T phi[Q], const T h[Q], const Collide<T> &p,
-                                            T b[Q], T &jx, T &jy, T &jz) {
+__device__ __forceinline__ void shifted_j(const T h[Q], const Collide<T> &p, T &jx, T &jy, T &jz) {
+    jx = h[1] - h[2] + h[7] - h[8] + h[9] - h[10] + h[11] - h[12] + h[13] - h[14] + T(0.5) * p.Fx;
+    jy = h[3] - h[4] + h[7] - h[8] - h[9] + h[10] + h[15] - h[16] + h[17] - h[18] + T(0.5) * p.Fy;
+    jz = h[5] - h[6] + h[11] - h[12] - h[13] + h[14] + h[15] - h[16] - h[17] + h[18] + T(0.5) * p.Fz;
+}
+
+// b = D^-1 M phi (phi the streamed-back adjoint at the node).
+template <typename T>
+__device__ __forceinline__ void adj_moments(const T phi[Q], T b[Q]) {
     T a[Q];
     moments_of<T>(phi, a);
 #pragma unroll
     for (int k = 0; k < Q; ++k) b[k] = a[k] * inv_norm<T>(k);
-    jx = h[1] - h[2] + h[7] - h[8] + h[9] - h[10] + h[11] - h[12] + h[13] - h[14] + T(0.5) * p.Fx;
-    jy = h[3] - h[4] + h[7] - h[8] - h[9] + h[10] + h[15] - h[16] + h[17] - h[18] + T(0.5) * p.Fy;
-    jz = h[5] - h[6] + h[11] - h[12] - h[13] + h[14] + h[15] - h[16] - h[17] + h[18] + T(0.5) * p.Fz;
+}
+
+// J3 = the shifted momentum of H, component-major [3][units] (0 off fluid).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_j3(const T *__restrict__ H, AdjView v, Collide<T> p,
+                                                T *__restrict__ J3) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= v.units) return;
+    AdjUnit un;
+    un.init(u, v);
+    T jx = T(0), jy = T(0), jz = T(0);
+    if (un.fluid) {
+        T h[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) h[i] = H[(size_t)i * v.units + u];
+        shifted_j<T>(h, p, jx, jy, jz);
+    }
+    J3[u] = jx;
+    J3[(size_t)v.units + u] = jy;
+    J3[2 * (size_t)v.units + u] = jz;
 }
 
 // H = streamed state (average = 0) or H = (H + streamed state) / 2 (average = 1).
@@ -153,7 +180,9 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
 // before psi_in on entry; with `partials`, also the block sums of
 // |new - that iterate|^2 (a change over two iterations, blind to a period-2
 // component) and |new|^2.
-template <typename T>
+// The linearisation point comes as the full streamed state H (FROM_H) or as
+// its shifted momentum J3 alone (fewer bytes per iteration).
+template <typename T, bool FROM_H>
 __global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in,
                                                   T *__restrict__ psi_out, AdjView v, Collide<T> p,
                                                   T coef, int d, double *partials) {
@@ -163,7 +192,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const
         AdjUnit un;
         un.init(u, v);
         if (un.fluid) {
-            T phi[Q], h[Q], b[Q], c[Q];
+            T phi[Q], b[Q], c[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 // population i of x went downstream to x + c_i = x - c_opp(i)
@@ -171,10 +200,19 @@ __global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const
                 phi[i] = (i == 0 || (un.bits & (1u << o)))
                              ? psi_in[(size_t)(i == 0 ? 0 : o) * v.units + u]
                              : psi_in[(size_t)i * v.units + un.up(o, u, v)];
-                h[i] = H[(size_t)i * v.units + u];
             }
             T jx, jy, jz;
-            adj_moments<T>(phi, h, p, b, jx, jy, jz);
+            if (FROM_H) {
+                T h[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) h[i] = H[(size_t)i * v.units + u];
+                shifted_j<T>(h, p, jx, jy, jz);
+            } else {
+                jx = H[u];
+                jy = H[(size_t)v.units + u];
+                jz = H[2 * (size_t)v.units + u];
+            }
+            adj_moments<T>(phi, b);
             const T q = p.linear ? T(0) : T(1);
             T sb[Q], kb[Q];
 #pragma unroll
@@ -239,7 +277,8 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
                 h[i] = H[(size_t)i * v.units + u];
             }
             T jx, jy, jz;
-            adj_moments<T>(phi, h, p, b, jx, jy, jz);
+            shifted_j<T>(h, p, jx, jy, jz);
+            adj_moments<T>(phi, b);
             moments_of<T>(h, m);
             eq_and_force<T>(m[0], jx, jy, jz, p, meq, mF);
             double rk[Q];
@@ -346,16 +385,18 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
                        double sums[10], int64_t *iters, double *resid) {
     const AdjView v = make_adj_view(c);
     const size_t bytes = sizeof(T) * Q * (size_t)v.units;
-    T *H = nullptr, *cur = nullptr, *prev = nullptr;
+    T *H = nullptr, *cur = nullptr, *prev = nullptr, *J3 = nullptr;
     double *part = nullptr, *dsum = nullptr;
     const unsigned grid = (unsigned)((v.units + 255) / 256);
     cudaError_t e = cudaMalloc(&H, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&J3, sizeof(T) * 3 * (size_t)(v.units > 0 ? v.units : 1));
     if (e == cudaSuccess) e = cudaMalloc(&cur, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&prev, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 10 * (size_t)(grid > 0 ? grid : 1));
     if (e == cudaSuccess) e = cudaMalloc(&dsum, sizeof(double) * 10);
     auto cleanup = [&]() {
         cudaFree(H);
+        cudaFree(J3);
         cudaFree(cur);
         cudaFree(prev);
         cudaFree(part);
@@ -374,6 +415,9 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
         capture<T>(c, v, grid, H, 0);
         launch_step(c, false);
         capture<T>(c, v, grid, H, 1);
+        // the iteration needs the linearisation point only through its momentum
+        k_adj_j3<T><<<grid, 256, 0, c->stream>>>(H, v, p, J3);
+        c->launches++;
         // psi_{-1} = psi_0 = 0: the first step gives psi_1 = dJ/dh
         e = cudaMemsetAsync(cur, 0, bytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0, bytes, c->stream);
@@ -382,7 +426,7 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
         while (e == cudaSuccess && *iters < max_iter) {
             const bool check = *iters >= 1 && (((*iters + 1) % K == 0) || (*iters + 1 == max_iter));
             // prev <- J^T S^T cur + g (prev held the iterate before cur)
-            k_adj_step<T><<<grid, 256, 0, c->stream>>>(H, cur, prev, v, p, (T)coef, d,
+            k_adj_step<T, false><<<grid, 256, 0, c->stream>>>(J3, cur, prev, v, p, (T)coef, d,
                                                        check ? part : nullptr);
             c->launches++;
             T *t = cur;
@@ -493,7 +537,7 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
         e = cudaMemsetAsync(nxt, 0, sizeof(T) * fieldT, c->stream);
     }
     if (e == cudaSuccess) {
-        k_adj_step<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, psi, v, p, (T)coef, d, nullptr);
+        k_adj_step<T, true><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, psi, v, p, (T)coef, d, nullptr);
         k_adj_grad<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, nxt, v, p, d, part);
         k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10 * (size_t)n);
         c->launches += 3;
@@ -513,7 +557,7 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
             k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, part);
             k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid,
                                                           dsum + 10 * (size_t)t_global);
-            k_adj_step<T><<<grid, 256, 0, c->stream>>>(H, psi, nxt, v, p, (T)0, d, nullptr);
+            k_adj_step<T, true><<<grid, 256, 0, c->stream>>>(H, psi, nxt, v, p, (T)0, d, nullptr);
             c->launches += 3;
             T *tmp = psi;
             psi = nxt;
