@@ -555,7 +555,7 @@ def sweep_run(args, stream):
             "max_k_diff": float(np.max(np.abs(np.array(ks)[:, 0] - kb[:, 0]))),  # driven (x) component
             "k_bitwise_equal": bool(np.array_equal(np.array(ks)[:, 0], kb[:, 0])),
             "layouts": {"aa": int(np.sum(lay == 1)), "sparse": int(np.sum(lay == 2)),
-                        "npt2": int(np.sum(npt == 2))}}
+                        "npt2": int(np.sum(npt == 2)), "alone": int(np.sum(npt == 0))}}
 
 
 def adjoint_run(args, stream):

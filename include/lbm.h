@@ -304,6 +304,12 @@ typedef struct {
     int32_t test_skip_block;    /* test hook, default -1: block that skips its first barrier
                                    arrival, so the others' waits run out (LBM_ETIMEOUT) */
     int32_t stop_rule;          /* as lbm_options.stop_rule */
+    int32_t solo;               /* lattices whose layout and nodes per thread are
+                                   autotuned may run alone, with the single-lattice
+                                   kernels, where the autotuner times that faster
+                                   than the batched kernel (a lattice that fills the
+                                   GPU by itself): 1 (default) let it choose, 0 never,
+                                   2 always (every autotuned lattice runs alone) */
 } lbm_batch_options;
 
 typedef struct lbm_batch lbm_batch;
@@ -323,7 +329,8 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status);
  * the current states' mean velocities U[n][3]. */
 int lbm_batch_permeability(lbm_batch *b, double *k);
 int lbm_batch_mean_velocity(lbm_batch *b, double *U);
-/* Layout and nodes per thread chosen for each lattice (nullable outputs). */
+/* Layout and nodes per thread chosen for each lattice (nullable outputs);
+ * nodes_per_thread 0 marks a lattice that runs alone (see solo). */
 int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *nodes_per_thread);
 /* The context of lattice i (owned by the batch; valid until lbm_batch_destroy),
  * for the single-lattice readers (populations, velocity, checkpoint). */

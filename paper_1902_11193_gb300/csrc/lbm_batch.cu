@@ -38,6 +38,7 @@
 namespace lbm {
 
 SparseMap sparse_map(const lbm_ctx *c);
+int launch_step(lbm_ctx *c, bool reduce);
 
 struct BatchLat {
     int layout;  // LBM_LAYOUT_AA or LBM_LAYOUT_SPARSE
@@ -109,8 +110,14 @@ __device__ bool grid_sync(GridBar *bar, unsigned nblocks, uint64_t timeout_ns, b
     return ok != 0;
 }
 
+// Minimum resident blocks per SM of the batched kernel (caps its registers;
+// the cooperative grid is the resident-block count times the SM count).
+#ifndef LBM_BATCH_MIN_BLOCKS
+#define LBM_BATCH_MIN_BLOCKS 3
+#endif
+
 template <typename S>
-__global__ void __launch_bounds__(256) k_batch(const BatchLat *__restrict__ lats,
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_BATCH_MIN_BLOCKS) k_batch(const BatchLat *__restrict__ lats,
                                                const Tile *__restrict__ tiles,
                                                const int *__restrict__ ntiles_p,
                                                const int64_t *__restrict__ lat_steps, int nsteps,
@@ -229,6 +236,7 @@ struct lbm_batch {
     cudaStream_t stream;
     bool own_stream;
     std::vector<int> layout, npt;
+    std::vector<char> solo;  // run alone with the single-lattice kernels
     std::vector<char> active;
     std::vector<int64_t> steps;
     std::vector<int> status;
@@ -265,6 +273,7 @@ void lbm_batch_default_options(lbm_batch_options *o) {
     o->barrier_timeout_ms = 2000;
     o->test_skip_block = -1;
     o->stop_rule = 0;
+    o->solo = 1;
 }
 
 void lbm_batch_destroy(lbm_batch *b) {
@@ -415,6 +424,23 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
     return ms;
 }
 
+// Device time of `steps` single-lattice steps of context c on the batch's
+// stream (launch gaps included): the cost of running the lattice alone.
+float time_solo(lbm_batch *b, lbm_ctx *c, int steps) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = INFINITY;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        cudaEventRecord(e0, c->stream);
+        for (int t = 0; t < steps; ++t) launch_step(c, false);
+        cudaEventRecord(e1, c->stream);
+        if (cudaStreamSynchronize(c->stream) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    (void)b;
+    return ms;
+}
+
 std::string mask_key(const lbm_lattice_desc &d) {
     const size_t N = (size_t)d.dims[0] * d.dims[1] * d.dims[2];
     uint64_t h = 1469598103934665603ull;  // FNV-1a over the mask bytes
@@ -444,6 +470,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     if (o.barrier_timeout_ms <= 0) o.barrier_timeout_ms = 2000;
     if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
     if (o.stop_rule == 1 && o.check_interval < 3) o.check_interval = 3;
+    if (o.solo < 0 || o.solo > 2) return LBM_EINVAL;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ENOMEM;
     b->n = n;
@@ -493,12 +520,24 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                     if (rc != LBM_OK) return fail(rc);
                     for (int cn : {1, 2}) {
                         if (np != 0 && cn != np) continue;
+                        if (o.solo == 2) continue;
                         time_candidate(b, c, cn, 2);  // warm-up
                         const float ms = time_candidate(b, c, cn, 8);
                         if (ms < best) {
                             best = ms;
                             bl = cl;
                             bn = cn;
+                        }
+                    }
+                    // a lattice that fills the GPU alone may run faster
+                    // without the batch (bn = 0: run it alone)
+                    if (np == 0 && o.solo != 0) {
+                        time_solo(b, c, 2);  // warm-up
+                        const float ms = time_solo(b, c, 8);
+                        if (ms < best || o.solo == 2) {
+                            best = ms;
+                            bl = cl;
+                            bn = 0;
                         }
                     }
                     lbm_destroy(c);
@@ -510,6 +549,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
         }
         b->layout[i] = lay;
         b->npt[i] = np;
+        b->solo.push_back(np == 0);
         lbm_options to = lo;
         to.layout = lay;
         lbm_ctx *c = nullptr;
@@ -521,8 +561,8 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     std::vector<BatchLat> lats(n);
     int total_tiles = 0;
     for (int i = 0; i < n; ++i) {
-        lats[i] = make_lat(b->ctx[i], b->npt[i]);
-        total_tiles += ntiles_of(lats[i]);
+        lats[i] = make_lat(b->ctx[i], b->solo[i] ? 1 : b->npt[i]);
+        if (!b->solo[i]) total_tiles += ntiles_of(lats[i]);
     }
     b->max_tiles = total_tiles > 0 ? total_tiles : 1;
 #define CKB(call)                                        \
@@ -559,10 +599,13 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
     if (!b || !(tol >= 0.0)) return LBM_EINVAL;
     if (b->failed) return LBM_ETIMEOUT;
     std::vector<BatchLat> lats(b->n);
-    for (int i = 0; i < b->n; ++i) lats[i] = make_lat(b->ctx[i], b->npt[i]);
-    // every lattice starts a fresh stopping-rule run
+    for (int i = 0; i < b->n; ++i) lats[i] = make_lat(b->ctx[i], b->solo[i] ? 1 : b->npt[i]);
+    // every lattice starts a fresh stopping-rule run; lattices that run alone
+    // are not in the persistent kernel's tile table
+    int nsolo = 0;
     for (int i = 0; i < b->n; ++i) {
-        b->active[i] = 1;
+        b->active[i] = !b->solo[i];
+        nsolo += b->solo[i];
         b->status[i] = LBM_ENOTCONV;
         b->steps[i] = 0;
         b->ctx[i]->converged = b->ctx[i]->has_conv = false;
@@ -577,7 +620,7 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
     }
     const int64_t K = b->opt.check_interval;
     bool dirty = true;
-    int nact = b->n;
+    int nact = b->n - nsolo;
     while (nact > 0) {
         cudaError_t e;
         if (dirty) {
@@ -658,6 +701,19 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
                 dirty = true;
             }
         }
+    }
+    // lattices that run alone: the single-lattice path with the batch's rule
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->solo[i]) continue;
+        lbm_ctx *c = b->ctx[i];
+        c->opt.stop_rule = b->opt.stop_rule;
+        const int64_t l0 = c->launches;
+        int64_t st = 0;
+        const int rc = lbm_run_to_convergence(c, tol, &st);
+        b->launches += c->launches - l0;
+        if (rc != LBM_OK && rc != LBM_ENOTCONV && rc != LBM_EUNSTABLE) return rc;
+        b->steps[i] = st;
+        b->status[i] = rc;
     }
     for (int i = 0; i < b->n; ++i) {
         if (steps) steps[i] = b->steps[i];

@@ -55,7 +55,7 @@ class BatchOptions(C.Structure):
                 ("check_interval", C.c_int32), ("linear_eq", C.c_int32), ("max_steps", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
                 ("barrier_timeout_ms", C.c_int32), ("test_skip_block", C.c_int32),
-                ("stop_rule", C.c_int32)]
+                ("stop_rule", C.c_int32), ("solo", C.c_int32)]
 
 
 class Options(C.Structure):
@@ -351,11 +351,14 @@ class LBMBatch:
     """Many lattices stepped together by the batched persistent kernel
     (lbm_batch_*).  `lattices` is a list of dicts with keys mask, and either
     set_/tau/Lambda or rates_, and force.  layout None lets the autotuner pick
-    dense AA or sparse per distinct image; nodes_per_thread 0 likewise."""
+    dense AA or sparse per distinct image; nodes_per_thread 0 likewise, and
+    then a lattice may run alone with the single-lattice kernels where that is
+    faster (solo "auto"; "never", or "always" for every autotuned lattice)."""
 
     def __init__(self, lattices, precision="fp32", layout=None, nodes_per_thread=0,
                  check_interval=100, linear_eq=False, max_steps=1_000_000, stream=None,
-                 use_graph=True, barrier_timeout_ms=2000, test_skip_block=-1, stop_rule=0):
+                 use_graph=True, barrier_timeout_ms=2000, test_skip_block=-1, stop_rule=0,
+                 solo="auto"):
         self.masks = [np.ascontiguousarray(l["mask"], np.uint8) for l in lattices]
         n = len(lattices)
         descs = (LatticeDesc * n)()
@@ -387,6 +390,7 @@ class LBMBatch:
         o.barrier_timeout_ms = int(barrier_timeout_ms)
         o.test_skip_block = int(test_skip_block)
         o.stop_rule = int(stop_rule)
+        o.solo = {"never": 0, "auto": 1, "always": 2}[solo]
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         h = C.c_void_p()

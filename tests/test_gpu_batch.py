@@ -39,14 +39,19 @@ def _lattices(geom):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("layout,npt,rule", [("aa", 1, 0), ("sparse", 2, 1), (None, 0, 1)])
-def test_batch_bitwise_equals_single_runs(L, geom, precision, layout, npt, rule):
+@pytest.mark.parametrize("layout,npt,rule,solo", [("aa", 1, 0, "auto"), ("sparse", 2, 1, "auto"),
+                                                  (None, 0, 1, "auto"), (None, 0, 0, "always")])
+def test_batch_bitwise_equals_single_runs(L, geom, precision, layout, npt, rule, solo):
     lats = _lattices(geom)
     B = L.LBMBatch(lats, precision=precision, layout=layout, nodes_per_thread=npt,
-                   check_interval=20, max_steps=6000, stop_rule=rule)
+                   check_interval=20, max_steps=6000, stop_rule=rule, solo=solo)
     steps, status = B.run(1e-7)
     lay, nps = B.config()
-    assert set(lay.tolist()) <= {L.AA, L.SPARSE} and set(nps.tolist()) <= {1, 2}
+    assert set(lay.tolist()) <= {L.AA, L.SPARSE} and set(nps.tolist()) <= {0, 1, 2}
+    if solo == "always":
+        assert np.all(nps == 0)  # every lattice ran alone
+    elif npt:
+        assert np.all(nps == npt)
     if rule == 1:
         assert np.all(status == 0)
     kb = B.permeability()
@@ -81,7 +86,8 @@ def test_batch_retires_unstable_and_capped(L, geom):
     lats = _lattices(geom)[:2]
     lats.append(dict(mask=geom.sphere_array(16, "sc", c=0.2), set_="SRT", tau=0.5001,
                      force=(0.5, 0, 0)))
-    B = L.LBMBatch(lats, precision="fp32", layout="aa", check_interval=10, max_steps=300)
+    B = L.LBMBatch(lats, precision="fp32", layout="aa", check_interval=10, max_steps=300,
+                   solo="never")
     steps, status = B.run(0.0)  # tol 0: nothing converges
     assert status[2] == -5  # unstable
     assert status[0] == -4 and status[1] == -4 and steps[0] == 300
@@ -90,12 +96,12 @@ def test_batch_retires_unstable_and_capped(L, geom):
 def test_batch_barrier_timeout_is_reported(L, geom):
     lats = _lattices(geom)
     B = L.LBMBatch(lats, precision="fp32", layout="aa", check_interval=10,
-                   barrier_timeout_ms=200, test_skip_block=0)
+                   barrier_timeout_ms=200, test_skip_block=0, solo="never")
     rc = B.run(1e-7, raise_on_failure=False)
     assert rc == -6  # LBM_ETIMEOUT: the waits ran out, the kernel returned
     assert B.run(1e-7, raise_on_failure=False) == -6
     B.close()
     # the device is still usable
-    C2 = L.LBMBatch(lats[:2], precision="fp32", layout="aa", check_interval=10)
+    C2 = L.LBMBatch(lats[:2], precision="fp32", layout="aa", check_interval=10, solo="never")
     steps, status = C2.run(1e-7)
     assert np.all(status == 0)
