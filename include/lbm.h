@@ -305,11 +305,13 @@ typedef struct {
                                    arrival, so the others' waits run out (LBM_ETIMEOUT) */
     int32_t stop_rule;          /* as lbm_options.stop_rule */
     int32_t solo;               /* lattices whose layout and nodes per thread are
-                                   autotuned may run alone, with the single-lattice
-                                   kernels, where the autotuner times that faster
-                                   than the batched kernel (a lattice that fills the
-                                   GPU by itself): 1 (default) let it choose, 0 never,
-                                   2 always (every autotuned lattice runs alone) */
+                                   autotuned, and that fill the GPU by themselves (at
+                                   least four waves of the batched kernel's threads),
+                                   may run alone with the single-lattice kernels where
+                                   the autotuner times that faster than the batched
+                                   kernel: 1 (default) let it choose, 0 never, 2 always
+                                   (every autotuned lattice runs alone, whatever its
+                                   size) */
 } lbm_batch_options;
 
 typedef struct lbm_batch lbm_batch;

@@ -424,6 +424,15 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
     return ms;
 }
 
+// Smallest lattice (units) offered to run alone: four waves of the batched
+// kernel's resident threads.
+int64_t solo_min_units() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 4 * (int64_t)sms * LBM_BATCH_MIN_BLOCKS * kTileThreads;
+}
+
 // Device time of `steps` single-lattice steps of context c on the batch's
 // stream (launch gaps included): the cost of running the lattice alone.
 float time_solo(lbm_batch *b, lbm_ctx *c, int steps) {
@@ -530,8 +539,12 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                         }
                     }
                     // a lattice that fills the GPU alone may run faster
-                    // without the batch (bn = 0: run it alone)
-                    if (np == 0 && o.solo != 0) {
+                    // without the batch (bn = 0: run it alone).  Only such
+                    // lattices are candidates: timed by itself a small lattice
+                    // pays every grid barrier alone, which in the batch is
+                    // shared by all lattices
+                    const int64_t units = cl == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+                    if (np == 0 && (o.solo == 2 || (o.solo == 1 && units >= solo_min_units()))) {
                         time_solo(b, c, 2);  // warm-up
                         const float ms = time_solo(b, c, 8);
                         if (ms < best || o.solo == 2) {
