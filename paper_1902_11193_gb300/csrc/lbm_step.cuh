@@ -85,9 +85,18 @@ __device__ __forceinline__ void aa_sparse_update(S *A, const SparseMap &m, uint3
         SparseNode sn;
         sn.init_from(k, nb.x, nb.y, m);
         loc[0] = k;
+        // Warps with no node on the x faces (most of them) skip the periodic
+        // wrap cases; measured faster than one path with the wrap branches.
+        if (__any_sync(__activemask(), sn.xlo || sn.xhi)) {
 #pragma unroll
-        for (int j = 1; j < Q; ++j)
-            loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up(j, m);
+            for (int j = 1; j < Q; ++j)
+                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up(j, m);
+        } else {
+#pragma unroll
+            for (int j = 1; j < Q; ++j)
+                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k
+                                                : (Idx)opp(j) * Nf + sn.up_interior(j);
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < Q; ++j) loc[j] = (Idx)j * Nf + k;
