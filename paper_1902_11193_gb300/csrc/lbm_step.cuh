@@ -85,17 +85,17 @@ __device__ __forceinline__ void aa_sparse_update(S *A, const SparseMap &m, uint3
         SparseNode sn;
         sn.init_from(k, nb.x, nb.y, m);
         loc[0] = k;
-        // Warps with no node on the x faces (most of them) skip the periodic
-        // wrap cases; measured faster than one path with the wrap branches.
-        if (__any_sync(__activemask(), sn.xlo || sn.xhi)) {
+        // Interior formulas for every node, then the periodic wrap in x for
+        // the few nodes on the x faces; measured faster than one path that
+        // tests for the wrap in every direction.
+#pragma unroll
+        for (int j = 1; j < Q; ++j)
+            loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k
+                                            : (Idx)opp(j) * Nf + sn.up_interior(j);
+        if (sn.xlo || sn.xhi) {
 #pragma unroll
             for (int j = 1; j < Q; ++j)
-                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up(j, m);
-        } else {
-#pragma unroll
-            for (int j = 1; j < Q; ++j)
-                loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k
-                                                : (Idx)opp(j) * Nf + sn.up_interior(j);
+                if (cx(j) != 0 && !(sn.bits & (1u << j))) loc[j] = (Idx)opp(j) * Nf + sn.up(j, m);
         }
     } else {
 #pragma unroll
