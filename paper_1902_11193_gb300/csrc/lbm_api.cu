@@ -34,6 +34,14 @@ int launch_error(cudaError_t e) {
     snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
 }
+// The mask as uploaded at creation (the context keeps only the device copy).
+static int host_mask(lbm_ctx *c, std::vector<uint8_t> &m) {
+    m.resize((size_t)c->N);
+    cudaError_t e = cudaMemcpyAsync(m.data(), c->d_mask, (size_t)c->N, cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return launch_error(e);
+}
 }  // namespace lbm
 
 using namespace lbm;
@@ -117,7 +125,6 @@ static void free_ctx(lbm_ctx *c) {
     cudaFree(c->d_flag);
     cudaFreeHost(c->h_U);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-    free(c->h_mask);
     delete c;
 }
 
@@ -169,11 +176,21 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
                          !(o.rho_in > 0.0) || !(o.rho_out > 0.0) || !isfinite(o.rho_in) ||
                          !isfinite(o.rho_out)))
         return LBM_EINVAL;
+    // fluid count and value check in one branch-free pass (vectorised by the
+    // compiler; a 512^3 mask is 128 MiB of host memory)
     int64_t Nf = 0;
-    for (int64_t n = 0; n < N; ++n) {
-        if (mask[n] > 1) return LBM_EINVAL;
-        Nf += mask[n] == 0;
+    uint32_t bits = 0;
+    for (int64_t b = 0; b < N; b += 65536) {
+        const int64_t e = N - b < 65536 ? N : b + 65536;
+        uint32_t cnt = 0;
+        for (int64_t n = b; n < e; ++n) {
+            const uint32_t v = mask[n];
+            bits |= v;
+            cnt += v == 0u;
+        }
+        Nf += cnt;
     }
+    if (bits > 1u) return LBM_EINVAL;
 
     lbm_ctx *c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ENOMEM;
@@ -189,12 +206,6 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     c->set = -1;
     c->Lambda = NAN;
     c->converged = false;
-    c->h_mask = (uint8_t *)malloc((size_t)N);
-    if (!c->h_mask) {
-        delete c;
-        return LBM_ENOMEM;
-    }
-    memcpy(c->h_mask, mask, (size_t)N);
 
     int rc = LBM_OK;
     auto fail = [&](int code) {
@@ -589,8 +600,11 @@ int lbm_get_populations(lbm_ctx *c, double *f) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_f);
     if (e != cudaSuccess) return launch_error(e);
+    std::vector<uint8_t> mask;
+    int rc = host_mask(c, mask);
+    if (rc != LBM_OK) return rc;
     for (int64_t n = 0; n < c->N; ++n)
-        if (c->h_mask[n])
+        if (mask[(size_t)n])
             for (int i = 0; i < 19; ++i) f[(size_t)i * c->N + n] = weight(i);
     return LBM_OK;
 }
@@ -693,6 +707,9 @@ struct CkptDomain {
 
 int lbm_save(lbm_ctx *c, const char *path) {
     if (!c || !path) return LBM_EINVAL;
+    std::vector<uint8_t> mask;
+    const int mrc = host_mask(c, mask);
+    if (mrc != LBM_OK) return mrc;
     const int64_t units = c->opt.layout == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
     const size_t bytes = c->elem * 19 * (size_t)units;
     std::vector<unsigned char> buf(bytes);
@@ -725,7 +742,7 @@ int lbm_save(lbm_ctx *c, const char *path) {
     CkptDomain dm{c->opt.pressure_x, c->opt.symmetry, c->opt.rho_in, c->opt.rho_out,
                   c->opt.collision, 0};
     bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&dm, sizeof dm, 1, fp) == 1 &&
-              fwrite(c->h_mask, 1, (size_t)c->N, fp) == (size_t)c->N &&
+              fwrite(mask.data(), 1, (size_t)c->N, fp) == (size_t)c->N &&
               (bytes == 0 || fwrite(buf.data(), 1, bytes, fp) == bytes);
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBM_OK : LBM_EIO;

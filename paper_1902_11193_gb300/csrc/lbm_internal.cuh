@@ -222,7 +222,6 @@ struct lbm_ctx {
     int *d_flag;          // non-finite flag
     double *h_U;          // pinned [8*3 + 2]
     int64_t launches;
-    uint8_t *h_mask;      // host copy of the mask [N]
     int set;              // lbm_set of the rates, -1 when given directly
     double Lambda;        // Set E magic parameter
     bool converged;       // the stopping rule held and the state has not moved since

@@ -116,11 +116,11 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *count, uin
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Writes fluid_idx, the node -> fluid map (-1 for solids), the fluid-index
-// base of every 32-voxel row word and the row starts.
+// Writes fluid_idx, the fluid-index base of every 32-voxel row word and the
+// row starts.
 __global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ mask, uint32_t N,
                                                   const uint32_t *__restrict__ offset,
-                                                  int32_t *fidx, int32_t *node2fluid, int Lx,
+                                                  int32_t *fidx, int Lx,
                                                   int Wr, uint32_t nrows, RowWord *rw,
                                                   int32_t *rstart) {
     const uint32_t n = blockIdx.x * 1024u + threadIdx.x;
@@ -142,12 +142,7 @@ __global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ ma
     if (n < N) {
         // fluid nodes before n in node order = fluid index of n if fluid
         const uint32_t k = offset[blockIdx.x] + sm[wid] + __popc(b & ((1u << lane) - 1u));
-        if (f) {
-            fidx[k] = (int32_t)n;
-            node2fluid[n] = (int32_t)k;
-        } else {
-            node2fluid[n] = -1;
-        }
+        if (f) fidx[k] = (int32_t)n;
         const uint32_t R = n / (uint32_t)Lx;
         const uint32_t x = n - R * (uint32_t)Lx;
         if ((x & 31u) == 0) rw[(size_t)R * Wr + (x >> 5)].base = (int32_t)k;
@@ -182,7 +177,7 @@ __global__ void k_sparse_nbr(SparseMap m, uint32_t Nf, int32_t *nbr) {
 }
 
 __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, int Lx, int Ly,
-                               int Lz, const int32_t *__restrict__ node2fluid, uint32_t *bb,
+                               int Lz, const uint8_t *__restrict__ mask, uint32_t *bb,
                                uint2 *nb, unsigned long long *links) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bits = 0;
@@ -191,7 +186,7 @@ __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, in
         const uint32_t n = (uint32_t)fidx[k];
 #pragma unroll
         for (int j = 1; j < Q; ++j) {
-            if (node2fluid[upstream(n, j, Lx, Ly, Lz)] < 0) bits |= 1u << j;
+            if (mask[upstream(n, j, Lx, Ly, Lz)] != 0) bits |= 1u << j;
         }
         bb[k] = bits;
         nb[k] = make_uint2(n, bits);
@@ -213,33 +208,26 @@ int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
     const uint32_t N = (uint32_t)c->N;
     const uint32_t nb = (N + 1023) / 1024;
     uint32_t *d_cnt = nullptr, *d_off = nullptr, *d_tot = nullptr;
-    int32_t *d_n2f = nullptr;
     cudaError_t e = cudaMalloc(&d_cnt, sizeof(uint32_t) * (2 * (size_t)nb + 1));
     if (e != cudaSuccess) return launch_error(e);
     d_off = d_cnt + nb;
     d_tot = d_off + nb;
-    e = cudaMalloc(&d_n2f, sizeof(int32_t) * (size_t)N);
-    if (e != cudaSuccess) {
-        cudaFree(d_cnt);
-        return launch_error(e);
-    }
     k_count_fluid<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_cnt);
     k_scan_counts<<<1, 1024, 0, c->stream>>>(d_cnt, nb, d_off, d_tot);
     const uint32_t nrows = (uint32_t)c->Ly * (uint32_t)c->Lz;
     const uint32_t nwords = nrows * (uint32_t)c->Wr;
     k_row_bits<<<(nwords + 255) / 256, 256, 0, c->stream>>>(c->d_mask, c->Lx, c->Wr, nwords, c->d_rw);
-    k_compact<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_off, c->d_fidx, d_n2f, c->Lx, c->Wr,
+    k_compact<<<nb, 1024, 0, c->stream>>>(c->d_mask, N, d_off, c->d_fidx, c->Lx, c->Wr,
                                           nrows, c->d_rw, c->d_rstart);
     const uint32_t Nf = (uint32_t)c->Nf;
     if (Nf > 0)
         k_sparse_links<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_fidx, Nf, c->Lx, c->Ly, c->Lz,
-                                                                 d_n2f, c->d_bb, c->d_nb, d_links);
+                                                                 c->d_mask, c->d_bb, c->d_nb, d_links);
     c->launches += 5;
     uint32_t tot = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(d_n2f);
     cudaFree(d_cnt);
     if (e != cudaSuccess) return launch_error(e);
     if ((int64_t)tot != c->Nf) return LBM_ECUDA;
