@@ -163,26 +163,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_BATCH_MIN_BLOCKS
                                  : aa_dense_update<S, false, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz);
                     }
                 }
-                if (slot >= 0) {
-                    // the single-lattice block reduction, term for term
-                    double v[3] = {fl ? (double)jx : 0.0, fl ? (double)jy : 0.0,
-                                   fl ? (double)jz : 0.0};
-                    __shared__ double sm[32][3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
-                    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) sm[threadIdx.x >> 5][a] = v[a];
-                    __syncthreads();
-                    if (threadIdx.x < 3) {
-                        double acc = 0.0;
-                        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += sm[w][threadIdx.x];
-                        tile_part[((size_t)slot * 2 * max_tiles + 2 * (size_t)t + r) * 3 + threadIdx.x] = acc;
-                    }
-                    __syncthreads();
-                }
+                if (slot >= 0)  // the single-lattice block reduction
+                    block_momentum_sum<C>(
+                        jx, jy, jz, fl,
+                        tile_part + ((size_t)slot * 2 * max_tiles + 2 * (size_t)t + r) * 3,
+                        nullptr);
             }
         }
         if (s + 1 < nsteps && !grid_sync(bar, gridDim.x, timeout_ns, s == 0 && skip_me)) return;

@@ -28,29 +28,11 @@ namespace lbm {
 
 // ---------------------------------------------------------------- helpers
 
+// Per-block partial sums of the momenta into red.partials[3 * blockIdx.x ..].
 template <typename C>
 __device__ __forceinline__ void block_reduce_velocity(C jx, C jy, C jz, bool fluid,
                                                       const Reduce &red) {
-    double v[3] = {fluid ? (double)jx : 0.0, fluid ? (double)jy : 0.0, fluid ? (double)jz : 0.0};
-    if (fluid && !isfinite(v[0] + v[1] + v[2])) atomicOr(red.flag, 1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
-    __shared__ double sm[32][3];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        sm[wid][0] = v[0];
-        sm[wid][1] = v[1];
-        sm[wid][2] = v[2];
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        double acc = 0.0;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) acc += sm[w][threadIdx.x];
-        red.partials[3 * (size_t)blockIdx.x + threadIdx.x] = acc;
-    }
+    block_momentum_sum<C>(jx, jy, jz, fluid, red.partials + 3 * (size_t)blockIdx.x, red.flag);
 }
 
 // ---------------------------------------------------------------- AB pull
@@ -145,20 +127,28 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
 #define LBM_SPARSE_ODD_NPT 4
 #endif
 
-template <typename S, typename Idx, int NPT, int K>
+// RED: also the per-256-node partial momentum sums of a measuring step
+// (partial g covers fluid nodes 256 g .. 256 g + 255, as in k_sparse).
+template <typename S, typename Idx, int NPT, int K, bool RED>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCKS)
     k_sparse_odd_t(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
-                   float ld_scale, float st_scale) {
+                   float ld_scale, float st_scale, Reduce red) {
     using C = typename Store<S>::C;
     uint32_t k = blockIdx.x * (256u * NPT) + threadIdx.x;
     uint2 nxt = k < Nf ? __ldg(m.nb + k) : make_uint2(0u, 0u);
 #pragma unroll 1
     for (int r = 0; r < NPT; ++r, k += 256u) {
-        if (k >= Nf) break;
+        const uint32_t group = blockIdx.x * (uint32_t)NPT + (uint32_t)r;
+        if (RED ? group * 256u >= Nf : k >= Nf) break;  // block-uniform when RED
+        const bool valid = k < Nf;
         const uint2 cur = nxt;
         if (r + 1 < NPT && k + 256u < Nf) nxt = __ldg(m.nb + k + 256u);
-        C jx, jy, jz;
-        aa_sparse_update<S, true, Idx, Store<S>, K>(A, m, Nf, k, cur, p, ld_scale, st_scale, jx, jy, jz);
+        C jx = C(0), jy = C(0), jz = C(0);
+        if (valid)
+            aa_sparse_update<S, true, Idx, Store<S>, K>(A, m, Nf, k, cur, p, ld_scale, st_scale,
+                                                        jx, jy, jz);
+        if (RED)
+            block_momentum_sum<C>(jx, jy, jz, valid, red.partials + 3 * (size_t)group, red.flag);
     }
 }
 
@@ -166,10 +156,10 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCK
 // thread, 256 apart, with the loads of both issued before either collision.
 // At two blocks per SM this keeps about a third more bytes in flight than one
 // node per thread at three blocks per SM (1.31 -> 1.25 ms at 512^3).
-template <typename S, int K>
+template <typename S, int K, bool RED>
 __global__ void __launch_bounds__(256, 2)
     k_sparse_even_x2(S *A, uint32_t Nf, Collide<typename Store<S>::C> p, float ld_scale,
-                     float st_scale) {
+                     float st_scale, Reduce red) {
     using C = typename Store<S>::C;
     const uint32_t k0 = blockIdx.x * 512u + threadIdx.x, k1 = k0 + 256u;
     const bool v0 = k0 < Nf, v1 = k1 < Nf;
@@ -178,16 +168,22 @@ __global__ void __launch_bounds__(256, 2)
     for (int j = 0; j < Q; ++j) g0[j] = v0 ? Store<S>::ld(A + (uint32_t)j * Nf + k0, ld_scale) : C(0);
 #pragma unroll
     for (int j = 0; j < Q; ++j) g1[j] = v1 ? Store<S>::ld(A + (uint32_t)j * Nf + k1, ld_scale) : C(0);
-    C jx, jy, jz;
+    C jx0 = C(0), jy0 = C(0), jz0 = C(0), jx1 = C(0), jy1 = C(0), jz1 = C(0);
     if (v0) {
-        collide_as<K, C>(g0, p, jx, jy, jz);
+        collide_as<K, C>(g0, p, jx0, jy0, jz0);
 #pragma unroll
         for (int j = 0; j < Q; ++j) Store<S>::st(A + (uint32_t)j * Nf + k0, g0[opp(j)], st_scale);
     }
     if (v1) {
-        collide_as<K, C>(g1, p, jx, jy, jz);
+        collide_as<K, C>(g1, p, jx1, jy1, jz1);
 #pragma unroll
         for (int j = 0; j < Q; ++j) Store<S>::st(A + (uint32_t)j * Nf + k1, g1[opp(j)], st_scale);
+    }
+    if (RED) {  // partials 2b and 2b + 1 (nodes 256 g .. 256 g + 255, as in k_sparse)
+        block_momentum_sum<C>(jx0, jy0, jz0, v0, red.partials + 3 * (size_t)(2 * blockIdx.x), red.flag);
+        if ((2 * blockIdx.x + 1) * 256u < Nf)  // block-uniform
+            block_momentum_sum<C>(jx1, jy1, jz1, v1, red.partials + 3 * (size_t)(2 * blockIdx.x + 1),
+                                  red.flag);
     }
 }
 
@@ -432,38 +428,49 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
     default:
         grid = nblocks(c->Nf, bs);
         if (grid == 0) break;
+        // measuring steps write one partial per 256 fluid nodes
+        const unsigned groups = (unsigned)((c->Nf + 255) / 256);
         if constexpr (sizeof(S) <= 4) {
-            if (!odd && !reduce && 19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
-                grid = (unsigned)((c->Nf + 511) / 512);
-                k_sparse_even_x2<S, K><<<grid, 256, 0, c->stream>>>(
-                    (S *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts);
+            if (!odd && 19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+                const unsigned g2 = (unsigned)((c->Nf + 511) / 512);
+                if (reduce)
+                    k_sparse_even_x2<S, K, true><<<g2, 256, 0, c->stream>>>(
+                        (S *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                else
+                    k_sparse_even_x2<S, K, false><<<g2, 256, 0, c->stream>>>(
+                        (S *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                grid = reduce ? groups : g2;
                 break;
             }
         }
-        if (odd && !reduce) {
+        if (odd) {
             const unsigned tg = (unsigned)((c->Nf + 256 * LBM_SPARSE_ODD_NPT - 1) /
                                            (256 * LBM_SPARSE_ODD_NPT));
-            if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32))
-                k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT, K><<<tg, 256, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
-            else
-                k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT, K><<<tg, 256, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts);
-            grid = tg;
-        } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
-            if (odd)
-                k_sparse<S, true, uint32_t, K><<<grid, bs, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
-            else
-                k_sparse<S, false, uint32_t, K><<<grid, bs, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+            const SparseMap sm = sparse_map(c);
+            S *A = (S *)c->d_pop[0];
+            const uint32_t Nf = (uint32_t)c->Nf;
+            if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+                if (reduce)
+                    k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT, K, true>
+                        <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
+                else
+                    k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT, K, false>
+                        <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
+            } else {
+                if (reduce)
+                    k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT, K, true>
+                        <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
+                else
+                    k_sparse_odd_t<S, size_t, LBM_SPARSE_ODD_NPT, K, false>
+                        <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
+            }
+            grid = reduce ? groups : tg;
+        } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {  // even steps, FP64 storage
+            k_sparse<S, false, uint32_t, K><<<grid, bs, 0, c->stream>>>(
+                (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
         } else {
-            if (odd)
-                k_sparse<S, true, size_t, K><<<grid, bs, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
-            else
-                k_sparse<S, false, size_t, K><<<grid, bs, 0, c->stream>>>(
-                    (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
+            k_sparse<S, false, size_t, K><<<grid, bs, 0, c->stream>>>(
+                (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
         }
         break;
     }

@@ -15,6 +15,66 @@
 
 namespace lbm {
 
+// Sum of the momenta (jx, jy, jz) of a block's units, one unit per thread,
+// written by threads 0..2 to out[0..2]; raises bit 0 of *flag (if given) on
+// a non-finite momentum.  Every thread of the block calls it (it synchronises
+// the block).  The order is fixed, so the result is reproducible, and the
+// single-lattice and batched kernels share it, so they agree bit for bit.
+//
+// FP64 arithmetic is scarce on this GPU (a shuffle tree in FP64 cost about
+// 1.3 ms per 5e7 units), so FP32 momenta are summed per warp in FP32 with
+// the exact error of every addition carried along (Knuth's two-sum): the
+// warp's sum is hi + lo to about 2^-48 relative.  Only the warp sums and the
+// block total are formed in FP64.  FP64 momenta use the same tree in FP64.
+__device__ __forceinline__ void two_sum_step(float &s, float &e, int o) {
+    const float ts = __shfl_down_sync(0xffffffffu, s, o);
+    const float te = __shfl_down_sync(0xffffffffu, e, o);
+    const float x = __fadd_rn(s, ts);
+    const float z = __fsub_rn(x, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(x, z)), __fsub_rn(ts, z));
+    e = __fadd_rn(__fadd_rn(e, te), err);
+    s = x;
+}
+
+template <typename C>
+__device__ __forceinline__ double warp_momentum_sum(C v) {
+    if constexpr (sizeof(C) == 8) {
+        double d = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        return d;
+    } else {
+        float s = v, e = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) two_sum_step(s, e, o);
+        return (double)s + (double)e;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void block_momentum_sum(C jx, C jy, C jz, bool fluid, double *out,
+                                                   int *flag) {
+    if (flag && fluid && !(isfinite(jx) && isfinite(jy) && isfinite(jz))) atomicOr(flag, 1);
+    const C zero = C(0);
+    const double w[3] = {warp_momentum_sum<C>(fluid ? jx : zero),
+                         warp_momentum_sum<C>(fluid ? jy : zero),
+                         warp_momentum_sum<C>(fluid ? jz : zero)};
+    __shared__ double sm[32][3];
+    if ((threadIdx.x & 31) == 0) {
+        sm[threadIdx.x >> 5][0] = w[0];
+        sm[threadIdx.x >> 5][1] = w[1];
+        sm[threadIdx.x >> 5][2] = w[2];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double acc = 0.0;
+        const int nw = (int)(blockDim.x >> 5);
+        for (int i = 0; i < nw; ++i) acc += sm[i][threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+    __syncthreads();
+}
+
 struct DenseNode {
     int x, xm, xp;
     uint32_t row[3][3];  // Lx*(y' + Ly*z') for y' in {y-1, y, y+1}, z' likewise (wrapped)
