@@ -79,12 +79,19 @@ KERNEL_SOURCES = ("lbm_kernels.cu", "lbm_step.cuh", "lbm_collide.cuh", "lbm_spar
 
 
 def kernel_source_hash():
+    """Hash of the stream-collide sources with comments and blank lines
+    removed, so that a change to a comment keeps the measured traffic."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1902_11193_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1902_11193_gb300", "csrc", name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -24,7 +24,8 @@ namespace lbm {
 // FP64 arithmetic is scarce on this GPU (a shuffle tree in FP64 cost about
 // 1.3 ms per 5e7 units), so FP32 momenta are summed per warp in FP32 with
 // the exact error of every addition carried along (Knuth's two-sum): the
-// warp's sum is hi + lo to about 2^-48 relative.  Only the warp sums and the
+// warp's sum hi + lo is off by at most about 2^-43 of the sum of the
+// magnitudes (the 31 carried errors are themselves added in FP32).  Only the warp sums and the
 // block total are formed in FP64.  FP64 momenta use the same tree in FP64.
 __device__ __forceinline__ void two_sum_step(float &s, float &e, int o) {
     const float ts = __shfl_down_sync(0xffffffffu, s, o);
