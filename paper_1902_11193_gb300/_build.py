@@ -21,7 +21,7 @@ LBM_SO = os.path.join(LIBDIR, "liblbm_gb300.so")
 
 CUDA_SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_links.cu", "lbm_adjoint.cu", "lbm_batch.cu",
                 "lbm_noalloc.cu", "lbm_domain.cu"]
-CUDA_HEADERS = ["lbm_internal.cuh", "lbm_collide.cuh", "lbm_sparse.cuh", "lbm_step.cuh"]
+CUDA_HEADERS = ["lbm_internal.cuh", "lbm_ctx.h", "lbm_collide.cuh", "lbm_sparse.cuh", "lbm_step.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

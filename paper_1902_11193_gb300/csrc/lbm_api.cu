@@ -124,6 +124,8 @@ static void free_ctx(lbm_ctx *c) {
     cudaFree(c->d_U);
     cudaFree(c->d_flag);
     cudaFreeHost(c->h_U);
+    for (int g = 0; g < kChunkGraphs; ++g)
+        if (c->graphs[g].exec) cudaGraphExecDestroy(c->graphs[g].exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -341,6 +343,73 @@ static int measured_step(lbm_ctx *c, int slot) {
     return LBM_OK;
 }
 
+static void enqueue_chunk_direct(lbm_ctx *c, int64_t plain, int first, int nmeas) {
+    for (int64_t t = 0; t < plain; ++t) step_launch(c, false);
+    for (int m = 0; m < nmeas; ++m) measured_step(c, first + m);
+}
+
+// Longest chunk captured as a graph (launches); longer ones are enqueued
+// directly, where launch overhead is negligible anyway.
+constexpr int64_t kMaxGraphChunk = 4096;
+
+// Enqueues `plain` plain steps, then measuring steps into slots first ..
+// first + nmeas - 1.  A chunk of a given shape is captured once per context
+// as a CUDA graph and replayed afterwards: on small lattices, where a step
+// takes a few microseconds, the per-launch overhead otherwise dominates.
+// Falls back to direct launches where the stream cannot be captured (it is
+// being captured by the caller, or is the legacy default stream).
+static int enqueue_chunk(lbm_ctx *c, int64_t plain, int first, int nmeas) {
+    const int phase = c->opt.layout == LBM_LAYOUT_AB ? c->cur : (int)(c->steps & 1);
+    if (plain + nmeas < 2 || plain > kMaxGraphChunk) {
+        enqueue_chunk_direct(c, plain, first, nmeas);
+        return LBM_OK;
+    }
+    for (int g = 0; g < kChunkGraphs; ++g) {
+        ChunkGraph &G = c->graphs[g];
+        if (G.exec && G.plain == plain && G.first == first && G.nmeas == nmeas && G.phase == phase) {
+            CK(cudaGraphLaunch(G.exec, c->stream));
+            c->steps += plain + nmeas;
+            c->launches += G.dlaunches;
+            c->cur = G.cur_after;
+            return LBM_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+        cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        enqueue_chunk_direct(c, plain, first, nmeas);
+        return LBM_OK;
+    }
+    const int64_t steps0 = c->steps, launches0 = c->launches;
+    const int cur0 = c->cur;
+    enqueue_chunk_direct(c, plain, first, nmeas);
+    const int64_t dlaunches = c->launches - launches0;
+    const int cur_after = c->cur;
+    c->steps = steps0;  // nothing ran yet: the capture only recorded the chunk
+    c->launches = launches0;
+    c->cur = cur0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        enqueue_chunk_direct(c, plain, first, nmeas);
+        return LBM_OK;
+    }
+    ChunkGraph &G = c->graphs[c->next_graph];
+    c->next_graph = (c->next_graph + 1) % kChunkGraphs;
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G = ChunkGraph{exec, plain, first, nmeas, phase, dlaunches, cur_after};
+    CK(cudaGraphLaunch(exec, c->stream));
+    c->steps += plain + nmeas;
+    c->launches += dlaunches;
+    c->cur = cur_after;
+    return LBM_OK;
+}
+
 static int read_U(lbm_ctx *c, int nslots) {
     CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 3 * nslots, cudaMemcpyDeviceToHost,
                        c->stream));
@@ -375,10 +444,8 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
                 done += chunk;
                 break;
             }
-            for (int64_t t = 0; t < chunk - 3; ++t) step_launch(c, false);
-            measured_step(c, 0);
-            measured_step(c, 1);
-            measured_step(c, 2);
+            rr = enqueue_chunk(c, chunk - 3, 0, 3);
+            if (rr) return rr;
             CK(cudaGetLastError());
             rr = read_U(c, 3);
             if (rr) return rr;
@@ -398,9 +465,8 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
             continue;
         }
         if (K >= 2 && chunk >= 2) {
-            for (int64_t t = 0; t < chunk - 2; ++t) step_launch(c, false);
-            measured_step(c, 0);
-            measured_step(c, 1);
+            rr = enqueue_chunk(c, chunk - 2, 0, 2);
+            if (rr) return rr;
             CK(cudaGetLastError());
             rr = read_U(c, 2);
             if (rr) return rr;

@@ -190,41 +190,6 @@ int launch_error(cudaError_t e);
 
 }  // namespace lbm
 
-struct lbm_ctx {
-    int Lx, Ly, Lz;
-    int64_t N, Nf;
-    double s[19];
-    double tau;  // 1/s_nu
-    double F[3];
-    lbm_options opt;
-    cudaStream_t stream;
-    bool own_stream;
-    int device;
+// The host-side context (device pointers, options, counters).
+#include "lbm_ctx.h"
 
-    uint8_t *d_mask;      // [N]
-    uint32_t *d_lw;       // [N] dense link words (AB, AA)
-    int32_t *d_fidx;      // [Nf] sparse: node index of each fluid node
-    uint32_t *d_bb;       // [Nf] sparse: bounceback bits
-    uint2 *d_nb;          // [Nf] sparse: {node index, bounceback bits} interleaved
-    lbm::RowWord *d_rw;   // [Ly*Lz][Wr] sparse: row fluid bits + fluid index base
-    int32_t *d_rstart;    // [Ly*Lz + 1] sparse: fluid index of each row's first node
-    int Wr;               // 32-voxel words per row
-    void *d_pop[2];       // populations; AB uses both, AA and SPARSE one
-    size_t elem;          // bytes per stored population value
-    float fp16_scale;     // 2^S (FP16 storage)
-    int cur;              // AB: index of the array holding the current state
-    int64_t steps;        // time steps taken
-    int64_t links[19];
-
-    double *d_partials;   // [max blocks][3]
-    int n_partial_blocks;
-    double *d_U;          // [8][3]: reduced mean velocities
-    int *d_flag;          // non-finite flag
-    double *h_U;          // pinned [8*3 + 2]
-    int64_t launches;
-    int set;              // lbm_set of the rates, -1 when given directly
-    double Lambda;        // Set E magic parameter
-    bool converged;       // the stopping rule held and the state has not moved since
-    bool has_conv;        // U_conv holds the measure of a finished stopping-rule run
-    double U_conv[3];     // the mean velocity that run stopped on
-};

@@ -32,15 +32,24 @@ __device__ __forceinline__ uint32_t upstream(uint32_t n, int j, int Lx, int Ly, 
     return (uint32_t)xs + (uint32_t)Lx * ((uint32_t)ys + (uint32_t)Ly * (uint32_t)zs);
 }
 
-// Adds the per-warp popcount of each direction's bounceback flag.
+// Adds the block's count of each direction's bounceback flag to links[j]:
+// warp popcounts into shared counters, then one global atomic per direction
+// and block (all 18 directions of every warp hitting the same 18 global
+// counters took 14 ms at 512^3).  Every thread of the block calls it.
 __device__ __forceinline__ void count_links(uint32_t bits, bool valid,
                                             unsigned long long *links) {
+    __shared__ unsigned cnt[Q];
+    if (threadIdx.x < Q) cnt[threadIdx.x] = 0u;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 1; j < Q; ++j) {
         unsigned b = __ballot_sync(0xffffffffu, valid && (bits & (1u << j)));
-        if (lane == 0 && b) atomicAdd(links + j, (unsigned long long)__popc(b));
+        if (lane == 0 && b) atomicAdd(&cnt[j], (unsigned)__popc(b));
     }
+    __syncthreads();
+    if (threadIdx.x > 0 && threadIdx.x < Q && cnt[threadIdx.x])
+        atomicAdd(links + threadIdx.x, (unsigned long long)cnt[threadIdx.x]);
 }
 
 // Dense link words.  Halfway mode: bounceback bits on fluid nodes, SOLID_BIT
