@@ -152,7 +152,10 @@ int lbm_step(lbm_ctx *ctx, int64_t n);
  * drive (the largest |F_j|) measured in the last two steps of a chunk.
  * *steps_taken (nullable) receives the steps run by this call.  Returns 0,
  * LBM_ENOTCONV after max_steps (state kept), LBM_EUNSTABLE on non-finite
- * values. */
+ * values.  Each chunk shape is captured once as a CUDA graph on the context
+ * stream and replayed (the context keeps up to four); where the stream is
+ * already being captured by the caller, chunks are launched directly.  Either
+ * way the results and the kernel-launch count are those of direct launches. */
 int lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t *steps_taken);
 
 /* Mean velocity U[3] of the current state after streaming (not advanced). */
