@@ -182,25 +182,59 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
 // component) and |new|^2.
 // The linearisation point comes as the full streamed state H (FROM_H) or as
 // its shifted momentum J3 alone (fewer bytes per iteration).
-template <typename T, bool FROM_H>
-__global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in,
+// SP: sparse layout (else dense AA/AB link words), a compile-time choice so
+// that each kernel carries only its own index arithmetic.  Sparse nodes use
+// the interior upstream formulas and redo the x-moving directions with the
+// periodic wrap only on the x faces (as the forward odd step does).
+// One unit per thread, four blocks per SM (FP32: 64 registers).  Tiles of
+// two or four units per thread, as the forward odd step uses, ran 3.5x
+// slower here.
+template <typename T, bool FROM_H, bool SP>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in,
                                                   T *__restrict__ psi_out, AdjView v, Collide<T> p,
                                                   T coef, int d, double *partials) {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     double r[2] = {0.0, 0.0};
     if (u < v.units) {
-        AdjUnit un;
-        un.init(u, v);
-        if (un.fluid) {
-            T phi[Q], b[Q], c[Q];
+        T phi[Q];
+        bool fluid = true;
+        // population i of x went downstream to x + c_i = x - c_opp(i), or
+        // bounced back into slot opp(i) of x
+        if (SP) {
+            SparseNode sn;
+            sn.init(u, v.sm);
+            phi[0] = psi_in[u];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                // population i of x went downstream to x + c_i = x - c_opp(i)
+            for (int i = 1; i < Q; ++i) {
                 const int o = opp(i);
-                phi[i] = (i == 0 || (un.bits & (1u << o)))
-                             ? psi_in[(size_t)(i == 0 ? 0 : o) * v.units + u]
-                             : psi_in[(size_t)i * v.units + un.up(o, u, v)];
+                phi[i] = (sn.bits & (1u << o)) ? psi_in[(size_t)o * v.units + u]
+                                               : psi_in[(size_t)i * v.units + sn.up_interior(o)];
             }
+            if (sn.xlo || sn.xhi) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int o = opp(i);
+                    if (cx(o) != 0 && !(sn.bits & (1u << o)))
+                        phi[i] = psi_in[(size_t)i * v.units + sn.up(o, v.sm)];
+                }
+            }
+        } else {
+            const uint32_t w = v.lw[u];
+            fluid = !(w & NOT_FLUID);
+            if (fluid) {
+                DenseNode dn;
+                dn.init(u, v.d);
+                phi[0] = psi_in[u];
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int o = opp(i);
+                    phi[i] = (w & (1u << o)) ? psi_in[(size_t)o * v.units + u]
+                                             : psi_in[(size_t)i * v.units + dn.up(o)];
+                }
+            }
+        }
+        if (fluid) {
+            T b[Q], c[Q];
             T jx, jy, jz;
             if (FROM_H) {
                 T h[Q];
@@ -246,6 +280,31 @@ __global__ void __launch_bounds__(256) k_adj_step(const T *__restrict__ H, const
         }
     }
     if (partials) block_sum_store<2>(r, partials);
+}
+
+// A captured chunk of the steady adjoint iteration, for one assignment of
+// the two iterate buffers (cur is where the chunk starts reading).
+struct AdjGraph {
+    cudaGraphExec_t exec = nullptr;
+    void *cur = nullptr;
+    int64_t dlaunches = 0;
+};
+
+// Blocks of k_adj_step for `units` units (also its number of partials).
+static unsigned adj_step_grid(uint32_t units) { return (units + 255u) / 256u; }
+
+template <typename T, bool FROM_H>
+void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, T *psi_out,
+                     const Collide<T> &p, T coef, int d, double *partials) {
+    const unsigned grid = adj_step_grid(v.units);
+    if (grid == 0) return;
+    if (v.layout == LBM_LAYOUT_SPARSE)
+        k_adj_step<T, FROM_H, true><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p, coef, d,
+                                                                 partials);
+    else
+        k_adj_step<T, FROM_H, false><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p, coef, d,
+                                                                  partials);
+    c->launches++;
 }
 
 // Per-node gradient contributions at the converged adjoint, with psi the
@@ -422,30 +481,103 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
         e = cudaMemsetAsync(cur, 0, bytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0, bytes, c->stream);
         const int64_t K = c->opt.check_interval > 0 ? c->opt.check_interval : 100;
+        const int nstep_part = (int)adj_step_grid(v.units);
         double host[2];
+        // A whole chunk of K iterations (the last one checking the residual)
+        // is captured once per pair of iterate buffers as a CUDA graph and
+        // replayed; K even needs one graph, K odd two.
+        AdjGraph graphs[2];
+        bool unstable = false;
         while (e == cudaSuccess && *iters < max_iter) {
+            if (K >= 2 && *iters % K == 0 && max_iter - *iters >= K) {
+                AdjGraph *G = nullptr;
+                for (AdjGraph &g : graphs)
+                    if (g.exec && g.cur == (void *)cur) G = &g;
+                if (!G) {
+                    AdjGraph &slot = graphs[graphs[0].exec ? 1 : 0];
+                    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+                    slot = AdjGraph{};
+                    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                    if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess &&
+                        cs == cudaStreamCaptureStatusNone &&
+                        cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) ==
+                            cudaSuccess) {
+                        const int64_t l0 = c->launches;
+                        T *a = cur, *b = prev;
+                        for (int64_t t = 0; t < K; ++t) {
+                            launch_adj_step<T, false>(c, v, J3, a, b, p, (T)coef, d,
+                                                      t + 1 == K ? part : nullptr);
+                            T *x = a;
+                            a = b;
+                            b = x;
+                        }
+                        k_sum_partials<2><<<1, 1024, 0, c->stream>>>(part, nstep_part, dsum);
+                        c->launches++;
+                        slot.dlaunches = c->launches - l0;
+                        c->launches = l0;
+                        cudaGraph_t graph = nullptr;
+                        cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+                        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&slot.exec, graph, 0);
+                        if (graph) cudaGraphDestroy(graph);
+                        if (ce != cudaSuccess) {
+                            cudaGetLastError();
+                            slot.exec = nullptr;
+                        } else {
+                            slot.cur = cur;
+                            G = &slot;
+                        }
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
+                if (G) {
+                    e = cudaGraphLaunch(G->exec, c->stream);
+                    if (e != cudaSuccess) break;
+                    c->launches += G->dlaunches;
+                    if (K % 2) {
+                        T *x = cur;
+                        cur = prev;
+                        prev = x;
+                    }
+                    *iters += K;
+                    e = cudaMemcpyAsync(host, dsum, sizeof host, cudaMemcpyDeviceToHost, c->stream);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                    if (e != cudaSuccess) break;
+                    *resid = host[1] > 0.0 ? sqrt(host[0] / host[1]) : 0.0;
+                    if (!isfinite(*resid)) {
+                        unstable = true;
+                        break;
+                    }
+                    if (*resid <= tol) break;
+                    continue;
+                }
+            }
             const bool check = *iters >= 1 && (((*iters + 1) % K == 0) || (*iters + 1 == max_iter));
             // prev <- J^T S^T cur + g (prev held the iterate before cur)
-            k_adj_step<T, false><<<grid, 256, 0, c->stream>>>(J3, cur, prev, v, p, (T)coef, d,
-                                                       check ? part : nullptr);
-            c->launches++;
+            launch_adj_step<T, false>(c, v, J3, cur, prev, p, (T)coef, d, check ? part : nullptr);
             T *t = cur;
             cur = prev;
             prev = t;
             ++*iters;
             if (check) {
-                k_sum_partials<2><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum);
+                k_sum_partials<2><<<1, 1024, 0, c->stream>>>(part, nstep_part, dsum);
                 c->launches++;
                 e = cudaMemcpyAsync(host, dsum, sizeof host, cudaMemcpyDeviceToHost, c->stream);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
                 if (e != cudaSuccess) break;
                 *resid = host[1] > 0.0 ? sqrt(host[0] / host[1]) : 0.0;
                 if (!isfinite(*resid)) {
-                    cleanup();
-                    return LBM_EUNSTABLE;
+                    unstable = true;
+                    break;
                 }
                 if (*resid <= tol) break;
             }
+        }
+        for (AdjGraph &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (unstable) {
+            cleanup();
+            return LBM_EUNSTABLE;
         }
         if (e == cudaSuccess) {
             k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, cur, prev, v, p, d, part);
@@ -537,10 +669,10 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
         e = cudaMemsetAsync(nxt, 0, sizeof(T) * fieldT, c->stream);
     }
     if (e == cudaSuccess) {
-        k_adj_step<T, true><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, psi, v, p, (T)coef, d, nullptr);
+        launch_adj_step<T, true>(c, v, Hbuf, nxt, psi, p, (T)coef, d, nullptr);
         k_adj_grad<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, nxt, v, p, d, part);
         k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10 * (size_t)n);
-        c->launches += 3;
+        c->launches += 2;
     }
     // reverse sweep, segment by segment
     int64_t t_global = n;
@@ -557,8 +689,8 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
             k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, part);
             k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid,
                                                           dsum + 10 * (size_t)t_global);
-            k_adj_step<T, true><<<grid, 256, 0, c->stream>>>(H, psi, nxt, v, p, (T)0, d, nullptr);
-            c->launches += 3;
+            launch_adj_step<T, true>(c, v, H, psi, nxt, p, (T)0, d, nullptr);
+            c->launches += 2;
             T *tmp = psi;
             psi = nxt;
             nxt = tmp;
