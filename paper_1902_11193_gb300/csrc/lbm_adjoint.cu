@@ -100,6 +100,30 @@ __device__ __forceinline__ void block_sum_store(double v[NV], double *partials) 
     }
 }
 
+// Block sums of (a, b) into partials[2 blockIdx.x ..]: the warp sums of the
+// momentum reduction (compensated FP32 for FP32, FP64 for FP64), then FP64.
+// The residual of the adjoint iteration only steers when to stop, so its
+// per-node terms are formed in the iteration's own precision; the FP64 form
+// (76 FP64 operations per node) made a checking launch eleven times as long
+// as a plain one on this GPU.
+template <typename T>
+__device__ __forceinline__ void block_sum2(T a, T b, double *partials) {
+    const double wa = warp_momentum_sum<T>(a), wb = warp_momentum_sum<T>(b);
+    __shared__ double sm[32][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm[wid][0] = wa;
+        sm[wid][1] = wb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double acc = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) acc += sm[w][threadIdx.x];
+        partials[2 * (size_t)blockIdx.x + threadIdx.x] = acc;
+    }
+}
+
 // Sum_k w_k dP_k/dv_a over the moments whose equilibrium (v = j), forcing
 // (v = F for d/du, v = u for d/dF) depends quadratically on the drive:
 // the derivative of (38 v.X, -11 v.X, 2(2 vx Xx - vy Xy - vz Xz), -m9/2,
@@ -189,12 +213,14 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
 // One unit per thread, four blocks per SM (FP32: 64 registers).  Tiles of
 // two or four units per thread, as the forward odd step uses, ran 3.5x
 // slower here.
-template <typename T, bool FROM_H, bool SP>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in,
-                                                  T *__restrict__ psi_out, AdjView v, Collide<T> p,
-                                                  T coef, int d, double *partials) {
+// CHK: a checking launch (residual partials); its own instantiation, so
+// that the plain launches carry none of its registers.
+template <typename T, bool FROM_H, bool SP, bool CHK>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
+    k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in, T *__restrict__ psi_out,
+               AdjView v, Collide<T> p, T coef, int d, double *partials) {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    double r[2] = {0.0, 0.0};
+    T r[2] = {T(0), T(0)};  // residual terms of this node, in the iteration's precision
     if (u < v.units) {
         T phi[Q];
         bool fluid = true;
@@ -247,6 +273,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_adj_step(const 
                 jz = H[2 * (size_t)v.units + u];
             }
             adj_moments<T>(phi, b);
+            // a checking launch compares with the iterate psi_out holds: its
+            // 19 values are loaded here, into phi (no longer needed), all at
+            // once; loaded next to their stores they made 19 dependent round
+            // trips per node
+            if (CHK) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) phi[i] = psi_out[(size_t)i * v.units + u];
+            }
             const T q = p.linear ? T(0) : T(1);
             T sb[Q], kb[Q];
 #pragma unroll
@@ -267,10 +301,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_adj_step(const 
                 const int ci = d == 0 ? cx(i) : (d == 1 ? cy(i) : cz(i));
                 const T val = out[i] + coef * T(ci);
                 T *dst = psi_out + (size_t)i * v.units + u;
-                if (partials) {
-                    const double dv = (double)val - (double)*dst;
+                if (CHK) {
+                    const T dv = val - phi[i];
                     r[0] += dv * dv;
-                    r[1] += (double)val * (double)val;
+                    r[1] += val * val;
                 }
                 *dst = val;
             }
@@ -279,7 +313,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_adj_step(const 
             for (int i = 0; i < Q; ++i) psi_out[(size_t)i * v.units + u] = T(0);
         }
     }
-    if (partials) block_sum_store<2>(r, partials);
+    if (CHK) block_sum2<T>(r[0], r[1], partials);
 }
 
 // A captured chunk of the steady adjoint iteration, for one assignment of
@@ -298,12 +332,22 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
                      const Collide<T> &p, T coef, int d, double *partials) {
     const unsigned grid = adj_step_grid(v.units);
     if (grid == 0) return;
-    if (v.layout == LBM_LAYOUT_SPARSE)
-        k_adj_step<T, FROM_H, true><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p, coef, d,
-                                                                 partials);
-    else
-        k_adj_step<T, FROM_H, false><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p, coef, d,
-                                                                  partials);
+    const bool sp = v.layout == LBM_LAYOUT_SPARSE;
+    if (partials) {
+        if (sp)
+            k_adj_step<T, FROM_H, true, true><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p,
+                                                                           coef, d, partials);
+        else
+            k_adj_step<T, FROM_H, false, true><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v,
+                                                                            p, coef, d, partials);
+    } else {
+        if (sp)
+            k_adj_step<T, FROM_H, true, false><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v,
+                                                                            p, coef, d, nullptr);
+        else
+            k_adj_step<T, FROM_H, false, false><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v,
+                                                                             p, coef, d, nullptr);
+    }
     c->launches++;
 }
 
