@@ -80,17 +80,18 @@ __device__ __forceinline__ size_t streamed_loc(const AdjState &st, const AdjView
     return (size_t)opp(j) * v.units + un.up(j, u, v);
 }
 
-template <int NV>
-__device__ __forceinline__ void block_sum_store(double v[NV], double *partials) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+// Block sums of NV values per thread into partials[NV blockIdx.x ..]: the
+// warp sums of the momentum reduction (compensated FP32 for FP32, FP64 for
+// FP64), then FP64 over the warps in order.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_n(const T x[NV], double *partials) {
     __shared__ double sm[32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
 #pragma unroll
-        for (int a = 0; a < NV; ++a) sm[wid][a] = v[a];
+    for (int a = 0; a < NV; ++a) {
+        const double w = warp_momentum_sum<T>(x[a]);
+        if (lane == 0) sm[wid][a] = w;
+    }
     __syncthreads();
     if (threadIdx.x < NV) {
         double acc = 0.0;
@@ -364,7 +365,10 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
                                                   const T *__restrict__ psi_b, AdjView v,
                                                   Collide<T> p, int d, double *partials) {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    double gsum[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // per-node terms in the iteration's precision (FP64 arithmetic is scarce
+    // on this GPU and this pass runs at every step of the transient
+    // adjoint); block sums as in block_sum_n
+    T gsum[10] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     if (u < v.units) {
         AdjUnit un;
         un.init(u, v);
@@ -384,10 +388,9 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
             adj_moments<T>(phi, b);
             moments_of<T>(h, m);
             eq_and_force<T>(m[0], jx, jy, jz, p, meq, mF);
-            double rk[Q];
+            T rk[Q];
 #pragma unroll
-            for (int k = 0; k < Q; ++k)
-                rk[k] = (double)b[k] * (-((double)m[k] - (double)meq[k]) - 0.5 * (double)mF[k]);
+            for (int k = 0; k < Q; ++k) rk[k] = b[k] * (-(m[k] - meq[k]) - T(0.5) * mF[k]);
             gsum[0] = rk[1];
             gsum[1] = rk[2];
             gsum[2] = rk[4] + rk[6] + rk[8];
@@ -403,16 +406,16 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
                 kb[k] = (T(1) - T(0.5) * s) * b[k];
             }
             const T ux = jx + T(0.5) * p.Fx, uy = jy + T(0.5) * p.Fy, uz = jz + T(0.5) * p.Fz;
-            gsum[6] = (double)(b[3] - T(2.0 / 3.0) * b[4] +
-                               q * (T(0.5) * dotP<T>(0, jx, jy, jz, sb) + dotP<T>(0, ux, uy, uz, kb)));
-            gsum[7] = (double)(b[5] - T(2.0 / 3.0) * b[6] +
-                               q * (T(0.5) * dotP<T>(1, jx, jy, jz, sb) + dotP<T>(1, ux, uy, uz, kb)));
-            gsum[8] = (double)(b[7] - T(2.0 / 3.0) * b[8] +
-                               q * (T(0.5) * dotP<T>(2, jx, jy, jz, sb) + dotP<T>(2, ux, uy, uz, kb)));
-            gsum[9] = (double)(d == 0 ? jx : (d == 1 ? jy : jz));
+            gsum[6] = b[3] - T(2.0 / 3.0) * b[4] +
+                      q * (T(0.5) * dotP<T>(0, jx, jy, jz, sb) + dotP<T>(0, ux, uy, uz, kb));
+            gsum[7] = b[5] - T(2.0 / 3.0) * b[6] +
+                      q * (T(0.5) * dotP<T>(1, jx, jy, jz, sb) + dotP<T>(1, ux, uy, uz, kb));
+            gsum[8] = b[7] - T(2.0 / 3.0) * b[8] +
+                      q * (T(0.5) * dotP<T>(2, jx, jy, jz, sb) + dotP<T>(2, ux, uy, uz, kb));
+            gsum[9] = d == 0 ? jx : (d == 1 ? jy : jz);
         }
     }
-    block_sum_store<10>(gsum, partials);
+    block_sum_n<T, 10>(gsum, partials);
 }
 
 // Fixed-order sum of NV-component partials by one block.
