@@ -52,6 +52,8 @@ def parse():
                    help="batched parameter sweep vs the same lattices one by one")
     p.add_argument("--adjoint", action="store_true", default=True)
     p.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    p.add_argument("--adjoint-size", type=int, default=128,
+                   help="edge of the adjoint leg's Boolean medium (r = 6, porosity 0.35)")
     p.add_argument("--large", action="store_true", default=True,
                    help="1024^3 low-porosity sparse leg, FP32 vs FP16 storage")
     p.add_argument("--no-large", dest="large", action="store_false")
@@ -566,14 +568,16 @@ def sweep_run(args, stream):
 
 
 def adjoint_run(args, stream):
-    """Steady adjoint on the 128^3 Boolean medium (r = 6, porosity 0.35):
-    FP32 forward to the paper's rule, then lbm_adjoint; gradients normalised."""
+    """Steady adjoint on a Boolean medium (r = 6, porosity 0.35, edge
+    --adjoint-size, 128 by default): FP32 forward to the paper's rule, then
+    lbm_adjoint; gradients normalised."""
     import torch
 
     from paper_1902_11193_gb300 import geometry, lbm
 
-    mask, _ = geometry.boolean(128, 6, 0.35, seed=1902_11193 + 4)
-    res = {"workload": "boolean-128^3 r=6 porosity=0.35, Set D tau=1, F=1e-6, fp32 sparse, "
+    L = args.adjoint_size
+    mask, _ = geometry.boolean(L, 6, 0.35, seed=1902_11193 + 4)
+    res = {"workload": f"boolean-{L}^3 r=6 porosity=0.35, Set D tau=1, F=1e-6, fp32 sparse, "
                        "two-step-mean stopping rule (tol 1e-8), adjoint tol 1e-6"}
     S = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision="fp32", layout="sparse",
                       check_interval=100, stream=stream, stop_rule=1, max_steps=200000)

@@ -234,8 +234,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int o = opp(i);
+                // on the x faces the interior index of an x-moving direction
+                // is wrong and may lie outside [0, units) (-1 or units at the
+                // ends of the fluid list): clamp it, so that this load stays
+                // in bounds; the value is replaced just below
+                uint32_t up = sn.up_interior(o);
+                if (cx(o) != 0) up = min(up, v.units - 1u);
                 phi[i] = (sn.bits & (1u << o)) ? psi_in[(size_t)o * v.units + u]
-                                               : psi_in[(size_t)i * v.units + sn.up_interior(o)];
+                                               : psi_in[(size_t)i * v.units + up];
             }
             if (sn.xlo || sn.xhi) {
 #pragma unroll
