@@ -52,6 +52,15 @@ def test_create_rejects_bad_arguments(L):
     bad[0, 0, 0] = 2
     with pytest.raises(L.LBMError):
         L.LBMSolver(bad, "B", tau=1.0)
+    # the mask check runs in blocks of 65536 voxels: bad values on either side
+    # of a block boundary and in the ragged last block are all caught
+    big = np.zeros((35, 40, 50), np.uint8)  # 70,000 voxels
+    for flat, val in ((65535, 2), (65536, 255), (big.size - 1, 3)):
+        bad = big.copy()
+        bad.reshape(-1)[flat] = val
+        with pytest.raises(L.LBMError) as e:
+            L.LBMSolver(bad, "B", tau=1.0)
+        assert e.value.code == -1
     with pytest.raises(L.LBMError):
         L.LBMSolver(m, "B", tau=1.0, block_size=48)
     s = L.rates("B", 1.0)
