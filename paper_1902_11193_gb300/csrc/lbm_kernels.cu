@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
 #define LBM_SPARSE_MIN_BLOCKS_EVEN 3
 #endif
 
-// Idx: type of the flat population offsets; uint32_t whenever 19 * Nf < 2^32.
+// One node per thread: the even steps of FP64 storage (the FP32 and FP16
+// steps use the tiled kernels below).  Idx: type of the flat population
+// offsets; uint32_t whenever 19 * Nf < 2^32.
 template <typename S, bool ODD, typename Idx, int K>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
                                        : (ODD ? LBM_SPARSE_MIN_BLOCKS : LBM_SPARSE_MIN_BLOCKS_EVEN))
@@ -115,14 +117,13 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
-// Odd steps without a velocity reduction: NPT nodes per thread.  A block
-// takes a tile of 256 * NPT consecutive fluid nodes and thread t the nodes
-// first + t, first + t + 256, ...; each node's {node index, bounceback bits}
-// record is loaded one node ahead, so that dependent fetch overlaps the
-// previous node's gathers and collision.  Steps that measure the mean
-// velocity use the one-node-per-thread kernel above.  (A persistent
-// grid-stride version of the same loop hides the index chain as well but
-// streams about a fifth slower; four nodes per thread measured best.)
+// Odd steps: NPT nodes per thread.  A block takes a tile of 256 * NPT
+// consecutive fluid nodes and thread t the nodes first + t, first + t + 256,
+// ...; each node's {node index, bounceback bits} record is loaded one node
+// ahead, so that dependent fetch overlaps the previous node's gathers and
+// collision.  (A persistent grid-stride version of the same loop hides the
+// index chain as well but streams about a fifth slower; four nodes per
+// thread measured best.)
 #ifndef LBM_SPARSE_ODD_NPT
 #define LBM_SPARSE_ODD_NPT 4
 #endif
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCK
     }
 }
 
-// Even steps without a velocity reduction, FP32 or FP16 storage: two nodes per
-// thread, 256 apart, with the loads of both issued before either collision.
+// Even steps, FP32 or FP16 storage: two nodes per thread, 256 apart, with
+// the loads of both issued before either collision.
 // At two blocks per SM this keeps about a third more bytes in flight than one
 // node per thread at three blocks per SM (1.31 -> 1.25 ms at 512^3).
 template <typename S, int K, bool RED>
