@@ -135,8 +135,10 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCK
     k_sparse_odd_t(S *A, SparseMap m, uint32_t Nf, Collide<typename Store<S>::C> p,
                    float ld_scale, float st_scale, Reduce red) {
     using C = typename Store<S>::C;
+    __shared__ double wsum[RED ? NPT : 1][8][3];  // RED: warp sums of each group
     uint32_t k = blockIdx.x * (256u * NPT) + threadIdx.x;
     uint2 nxt = k < Nf ? __ldg(m.nb + k) : make_uint2(0u, 0u);
+    int groups = 0;
 #pragma unroll 1
     for (int r = 0; r < NPT; ++r, k += 256u) {
         const uint32_t group = blockIdx.x * (uint32_t)NPT + (uint32_t)r;
@@ -148,8 +150,16 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : LBM_SPARSE_MIN_BLOCK
         if (valid)
             aa_sparse_update<S, true, Idx, Store<S>, K>(A, m, Nf, k, cur, p, ld_scale, st_scale,
                                                         jx, jy, jz);
-        if (RED)
-            block_momentum_sum<C>(jx, jy, jz, valid, red.partials + 3 * (size_t)group, red.flag);
+        if (RED) warp_momentum_store<C>(jx, jy, jz, valid, wsum[RED ? r : 0], red.flag);
+        ++groups;
+    }
+    if (RED) {  // one synchronisation for all of the tile's groups
+        __syncthreads();
+        if ((int)threadIdx.x < 3 * groups) {
+            const int r = threadIdx.x / 3, a = threadIdx.x % 3;
+            red.partials[3 * (size_t)(blockIdx.x * (uint32_t)NPT + (uint32_t)r) + a] =
+                group_momentum_total(wsum[r], a);
+        }
     }
 }
 
@@ -181,10 +191,15 @@ __global__ void __launch_bounds__(256, 2)
         for (int j = 0; j < Q; ++j) Store<S>::st(A + (uint32_t)j * Nf + k1, g1[opp(j)], st_scale);
     }
     if (RED) {  // partials 2b and 2b + 1 (nodes 256 g .. 256 g + 255, as in k_sparse)
-        block_momentum_sum<C>(jx0, jy0, jz0, v0, red.partials + 3 * (size_t)(2 * blockIdx.x), red.flag);
-        if ((2 * blockIdx.x + 1) * 256u < Nf)  // block-uniform
-            block_momentum_sum<C>(jx1, jy1, jz1, v1, red.partials + 3 * (size_t)(2 * blockIdx.x + 1),
-                                  red.flag);
+        __shared__ double wsum[2][8][3];
+        warp_momentum_store<C>(jx0, jy0, jz0, v0, wsum[0], red.flag);
+        warp_momentum_store<C>(jx1, jy1, jz1, v1, wsum[1], red.flag);
+        __syncthreads();
+        const int ng = (2 * blockIdx.x + 1) * 256u < Nf ? 2 : 1;
+        if ((int)threadIdx.x < 3 * ng) {
+            const int r = threadIdx.x / 3, a = threadIdx.x % 3;
+            red.partials[3 * (size_t)(2 * blockIdx.x + r) + a] = group_momentum_total(wsum[r], a);
+        }
     }
 }
 

@@ -52,6 +52,32 @@ __device__ __forceinline__ double warp_momentum_sum(C v) {
     }
 }
 
+// The two halves of block_momentum_sum, for kernels that reduce several
+// groups per block with one synchronisation: the warp sums of a group go to
+// sm[warp][0..2] (lane 0 writes); after a __syncthreads, thread a (< 3) of
+// any warp adds the group's warps in order.  Same arithmetic, same order.
+template <typename C>
+__device__ __forceinline__ void warp_momentum_store(C jx, C jy, C jz, bool fluid,
+                                                    double (*sm)[3], int *flag) {
+    if (flag && fluid && !(isfinite(jx) && isfinite(jy) && isfinite(jz))) atomicOr(flag, 1);
+    const C zero = C(0);
+    const double w0 = warp_momentum_sum<C>(fluid ? jx : zero);
+    const double w1 = warp_momentum_sum<C>(fluid ? jy : zero);
+    const double w2 = warp_momentum_sum<C>(fluid ? jz : zero);
+    if ((threadIdx.x & 31) == 0) {
+        sm[threadIdx.x >> 5][0] = w0;
+        sm[threadIdx.x >> 5][1] = w1;
+        sm[threadIdx.x >> 5][2] = w2;
+    }
+}
+
+__device__ __forceinline__ double group_momentum_total(const double (*sm)[3], int a) {
+    double acc = 0.0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int i = 0; i < nw; ++i) acc += sm[i][a];
+    return acc;
+}
+
 template <typename C>
 __device__ __forceinline__ void block_momentum_sum(C jx, C jy, C jz, bool fluid, double *out,
                                                    int *flag) {
