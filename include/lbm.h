@@ -58,7 +58,11 @@ typedef enum { LBM_SET_A = 0, LBM_SET_B, LBM_SET_C, LBM_SET_D, LBM_SET_E, LBM_SE
 /* Storage precision of the populations.  FP64 stores and computes in double;
  * FP32_SHIFTED stores f_i - w_i in float and computes in float;
  * FP16_SHIFTED stores 2^S (f_i - w_i) in half and computes in float.  Mean
- * velocities and residuals are always accumulated in double. */
+ * velocities and residuals are accumulated in double across warps.  Within a
+ * warp, float values are added in float with the exact rounding error of
+ * every addition carried along (a compensated sum, off by at most about
+ * 2^-43 of the sum of magnitudes); double values are added in double.  The
+ * order is fixed, so results are reproducible. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP16_SHIFTED = 2 } lbm_precision;
 
 /* AB: two population arrays, pull stream.  AA: one array, in-place AA
@@ -250,7 +254,9 @@ typedef struct {
  * derivative of eq. (perm_calc) at a converged state).  Solves
  * psi = J_C^T S^T psi + dk/dh in the context's precision (FP64 for FP64
  * storage, FP32 otherwise) with the residual checked every check_interval
- * iterations until <= tol or max_iter, then reduces the gradient in FP64.
+ * iterations until <= tol or max_iter, then reduces the gradient (per-node
+ * terms in that precision, sums as for the mean velocity).  The iterations
+ * between two checks are replayed from a CUDA graph on the context stream.
  * The state must be the converged one: LBM_ENOSTATE unless the last
  * lbm_run_to_convergence succeeded and nothing stepped or set the state
  * since.  The linearisation point is the mean of the streamed states of the
