@@ -83,7 +83,9 @@ __device__ __forceinline__ size_t streamed_loc(const AdjState &st, const AdjView
 // Block sums of NV values per thread into partials[NV blockIdx.x ..]: the
 // warp sums of the momentum reduction (compensated FP32 for FP32, FP64 for
 // FP64), then FP64 over the warps in order.
-template <typename T, int NV>
+// ADD: add the block's sums into partials instead of storing them (one
+// accumulator per block across the launches of a sweep).
+template <typename T, int NV, bool ADD = false>
 __device__ __forceinline__ void block_sum_n(const T x[NV], double *partials) {
     __shared__ double sm[32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -97,7 +99,8 @@ __device__ __forceinline__ void block_sum_n(const T x[NV], double *partials) {
         double acc = 0.0;
         const int nw = (blockDim.x + 31) >> 5;
         for (int w = 0; w < nw; ++w) acc += sm[w][threadIdx.x];
-        partials[(size_t)NV * blockIdx.x + threadIdx.x] = acc;
+        double &out = partials[(size_t)NV * blockIdx.x + threadIdx.x];
+        out = ADD ? out + acc : acc;
     }
 }
 
@@ -193,12 +196,21 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
     if (u >= v.units) return;
     AdjUnit un;
     un.init(u, v);
+    // all 19 loads before any store: H and A may alias as far as the
+    // compiler knows, so interleaved they made 19 dependent round trips
+    C val[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const C val = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
-        C *dst = H + (size_t)i * v.units + u;
-        *dst = average ? C(0.5) * (*dst + val) : val;
+    for (int i = 0; i < Q; ++i)
+        val[i] = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
+    if (average) {
+        C old[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) old[i] = H[(size_t)i * v.units + u];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) val[i] = C(0.5) * (old[i] + val[i]);
     }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) H[(size_t)i * v.units + u] = val[i];
 }
 
 // psi_out = J_C(h)^T S^T psi_in + coef c_{., d}.  psi_out holds the iterate
@@ -366,7 +378,9 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
 //        b_{j_a} - (2/3) b_{q_a} + q [ (1/2) dP_a(j; s b) + dP_a(j + F/2; (1 - s/2) b) ];
 // [9]    the drive component of sum_x (sum_i c_i h_i + F/2) (N times the mean
 //        velocity of the linearisation point).
-template <typename T>
+// ACC: add the block's sums into `partials` (the transient sweep keeps one
+// accumulator per block over all its steps).
+template <typename T, bool ACC = false>
 __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const T *__restrict__ psi_a,
                                                   const T *__restrict__ psi_b, AdjView v,
                                                   Collide<T> p, int d, double *partials) {
@@ -375,6 +389,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
     // on this GPU and this pass runs at every step of the transient
     // adjoint); block sums as in block_sum_n
     T gsum[10] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    const bool same = psi_a == psi_b;
     if (u < v.units) {
         AdjUnit un;
         un.init(u, v);
@@ -386,7 +401,8 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
                 const size_t at = (i == 0 || (un.bits & (1u << o)))
                                       ? (size_t)(i == 0 ? 0 : o) * v.units + u
                                       : (size_t)i * v.units + un.up(o, u, v);
-                phi[i] = T(0.5) * (psi_a[at] + psi_b[at]);
+                // psi_a == psi_b (the transient pass): 0.5 (x + x) is x exactly
+                phi[i] = same ? psi_a[at] : T(0.5) * (psi_a[at] + psi_b[at]);
                 h[i] = H[(size_t)i * v.units + u];
             }
             T jx, jy, jz;
@@ -421,7 +437,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
             gsum[9] = d == 0 ? jx : (d == 1 ? jy : jz);
         }
     }
-    block_sum_n<T, 10>(gsum, partials);
+    block_sum_n<T, 10, ACC>(gsum, partials);
 }
 
 // Fixed-order sum of NV-component partials by one block.
@@ -669,19 +685,21 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
     const size_t sbytes = c->elem * (size_t)Q * v.units;  // bytes of one population state
     T *Hbuf = nullptr, *psi = nullptr, *nxt = nullptr;
     unsigned char *ckpt = nullptr;
-    double *part = nullptr, *dsum = nullptr;
+    double *part = nullptr, *acc = nullptr, *dsum = nullptr;
     cudaError_t e = cudaMalloc(&Hbuf, sizeof(T) * fieldT * (size_t)C);
     if (e == cudaSuccess) e = cudaMalloc(&ckpt, sbytes * (size_t)(nseg + 1));
     if (e == cudaSuccess) e = cudaMalloc(&psi, sizeof(T) * fieldT);
     if (e == cudaSuccess) e = cudaMalloc(&nxt, sizeof(T) * fieldT);
     if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 10 * (size_t)grid);
-    if (e == cudaSuccess) e = cudaMalloc(&dsum, sizeof(double) * 10 * (size_t)(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&acc, sizeof(double) * 10 * (size_t)grid);
+    if (e == cudaSuccess) e = cudaMalloc(&dsum, sizeof(double) * 20);
     auto cleanup = [&]() {
         cudaFree(Hbuf);
         cudaFree(ckpt);
         cudaFree(psi);
         cudaFree(nxt);
         cudaFree(part);
+        cudaFree(acc);
         cudaFree(dsum);
     };
     if (e != cudaSuccess) {
@@ -724,11 +742,12 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
     if (e == cudaSuccess) {
         launch_adj_step<T, true>(c, v, Hbuf, nxt, psi, p, (T)coef, d, nullptr);
         k_adj_grad<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, nxt, v, p, d, part);
-        k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10 * (size_t)n);
+        k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10);
         c->launches += 2;
+        // the steps t < n add their block sums into acc, summed once at the end
+        e = cudaMemsetAsync(acc, 0, sizeof(double) * 10 * (size_t)grid, c->stream);
     }
     // reverse sweep, segment by segment
-    int64_t t_global = n;
     for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
         e = restore(sg);
         const int64_t len = (sg + 1) * C <= n ? C : n - sg * C;
@@ -738,12 +757,9 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
         }
         for (int64_t t = len - 1; t >= 0; --t) {
             const T *H = Hbuf + fieldT * (size_t)t;
-            --t_global;
-            k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, part);
-            k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid,
-                                                          dsum + 10 * (size_t)t_global);
+            k_adj_grad<T, true><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, acc);
             launch_adj_step<T, true>(c, v, H, psi, nxt, p, (T)0, d, nullptr);
-            c->launches += 2;
+            c->launches += 1;
             T *tmp = psi;
             psi = nxt;
             nxt = tmp;
@@ -751,15 +767,19 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = restore(nseg);
-    std::vector<double> host(10 * (size_t)(n + 1));
+    if (e == cudaSuccess) {
+        k_sum_partials<10><<<1, 1024, 0, c->stream>>>(acc, (int)grid, dsum);
+        c->launches++;
+    }
+    double host[20];
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(host.data(), dsum, sizeof(double) * host.size(), cudaMemcpyDeviceToHost,
-                            c->stream);
+        e = cudaMemcpyAsync(host, dsum, sizeof host, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) {
-        for (int64_t t = 0; t < n; ++t)
-            for (int a = 0; a < 9; ++a) sums[a] += host[10 * (size_t)t + a];
-        sums[9] = host[10 * (size_t)n + 9];
+        // steps t < n: components 0..8 summed over blocks and steps; step n
+        // contributes only N U_d of the final state (component 9)
+        for (int a = 0; a < 9; ++a) sums[a] = host[a];
+        sums[9] = host[10 + 9];
     }
     cleanup();
     return launch_error(e);
