@@ -380,7 +380,8 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
 //        velocity of the linearisation point).
 // ACC: add the block's sums into `partials` (the transient sweep keeps one
 // accumulator per block over all its steps).
-template <typename T, bool ACC = false>
+// SP: sparse layout (else dense), as in k_adj_step.
+template <typename T, bool ACC, bool SP>
 __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const T *__restrict__ psi_a,
                                                   const T *__restrict__ psi_b, AdjView v,
                                                   Collide<T> p, int d, double *partials) {
@@ -389,22 +390,54 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
     // on this GPU and this pass runs at every step of the transient
     // adjoint); block sums as in block_sum_n
     T gsum[10] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    // psi_a == psi_b (the transient pass): 0.5 (x + x) is x exactly
     const bool same = psi_a == psi_b;
+    auto psi_at = [&](size_t at) -> T {
+        return same ? psi_a[at] : T(0.5) * (psi_a[at] + psi_b[at]);
+    };
     if (u < v.units) {
-        AdjUnit un;
-        un.init(u, v);
-        if (un.fluid) {
-            T phi[Q], h[Q], b[Q], m[Q], meq[Q], mF[Q];
+        bool fluid = true;
+        T phi[Q];
+        // the value streamed back to u from direction i, as k_adj_step reads it
+        if (SP) {
+            SparseNode sn;
+            sn.init(u, v.sm);
+            phi[0] = psi_at(u);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
+            for (int i = 1; i < Q; ++i) {
                 const int o = opp(i);
-                const size_t at = (i == 0 || (un.bits & (1u << o)))
-                                      ? (size_t)(i == 0 ? 0 : o) * v.units + u
-                                      : (size_t)i * v.units + un.up(o, u, v);
-                // psi_a == psi_b (the transient pass): 0.5 (x + x) is x exactly
-                phi[i] = same ? psi_a[at] : T(0.5) * (psi_a[at] + psi_b[at]);
-                h[i] = H[(size_t)i * v.units + u];
+                uint32_t up = sn.up_interior(o);
+                if (cx(o) != 0) up = min(up, v.units - 1u);  // in bounds; x faces redone below
+                phi[i] = psi_at((sn.bits & (1u << o)) ? (size_t)o * v.units + u
+                                                     : (size_t)i * v.units + up);
             }
+            if (sn.xlo || sn.xhi) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int o = opp(i);
+                    if (cx(o) != 0 && !(sn.bits & (1u << o)))
+                        phi[i] = psi_at((size_t)i * v.units + sn.up(o, v.sm));
+                }
+            }
+        } else {
+            const uint32_t w = v.lw[u];
+            fluid = !(w & NOT_FLUID);
+            if (fluid) {
+                DenseNode dn;
+                dn.init(u, v.d);
+                phi[0] = psi_at(u);
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int o = opp(i);
+                    phi[i] = psi_at((w & (1u << o)) ? (size_t)o * v.units + u
+                                                    : (size_t)i * v.units + dn.up(o));
+                }
+            }
+        }
+        if (fluid) {
+            T h[Q], b[Q], m[Q], meq[Q], mF[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i] = H[(size_t)i * v.units + u];
             T jx, jy, jz;
             shifted_j<T>(h, p, jx, jy, jz);
             adj_moments<T>(phi, b);
@@ -438,6 +471,15 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
         }
     }
     block_sum_n<T, 10, ACC>(gsum, partials);
+}
+
+template <typename T, bool ACC>
+void launch_adj_grad(lbm_ctx *c, const AdjView &v, unsigned grid, const T *H, const T *psi_a,
+                     const T *psi_b, const Collide<T> &p, int d, double *partials) {
+    if (v.layout == LBM_LAYOUT_SPARSE)
+        k_adj_grad<T, ACC, true><<<grid, 256, 0, c->stream>>>(H, psi_a, psi_b, v, p, d, partials);
+    else
+        k_adj_grad<T, ACC, false><<<grid, 256, 0, c->stream>>>(H, psi_a, psi_b, v, p, d, partials);
 }
 
 // Fixed-order sum of NV-component partials by one block.
@@ -649,7 +691,7 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
             return LBM_EUNSTABLE;
         }
         if (e == cudaSuccess) {
-            k_adj_grad<T><<<grid, 256, 0, c->stream>>>(H, cur, prev, v, p, d, part);
+            launch_adj_grad<T, false>(c, v, grid, H, cur, prev, p, d, part);
             k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum);
             c->launches += 2;
             e = cudaMemcpyAsync(sums, dsum, sizeof(double) * 10, cudaMemcpyDeviceToHost, c->stream);
@@ -741,7 +783,7 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
     }
     if (e == cudaSuccess) {
         launch_adj_step<T, true>(c, v, Hbuf, nxt, psi, p, (T)coef, d, nullptr);
-        k_adj_grad<T><<<grid, 256, 0, c->stream>>>(Hbuf, nxt, nxt, v, p, d, part);
+        launch_adj_grad<T, false>(c, v, grid, Hbuf, nxt, nxt, p, d, part);
         k_sum_partials<10><<<1, 1024, 0, c->stream>>>(part, (int)grid, dsum + 10);
         c->launches += 2;
         // the steps t < n add their block sums into acc, summed once at the end
@@ -757,7 +799,7 @@ static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[
         }
         for (int64_t t = len - 1; t >= 0; --t) {
             const T *H = Hbuf + fieldT * (size_t)t;
-            k_adj_grad<T, true><<<grid, 256, 0, c->stream>>>(H, psi, psi, v, p, d, acc);
+            launch_adj_grad<T, true>(c, v, grid, H, psi, psi, p, d, acc);
             launch_adj_step<T, true>(c, v, H, psi, nxt, p, (T)0, d, nullptr);
             c->launches += 1;
             T *tmp = psi;
