@@ -187,21 +187,51 @@ __global__ void __launch_bounds__(256) k_adj_j3(const T *__restrict__ H, AdjView
 }
 
 // H = streamed state (average = 0) or H = (H + streamed state) / 2 (average = 1).
-template <typename S>
+// SP: sparse layout.  Its even-parity states keep every streamed value in
+// the node's own slots, so those captures need no index data; odd parity
+// uses the interior upstream formulas with the x faces redone, as the
+// adjoint step does.
+template <typename S, bool SP>
 __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjState st,
                                                      float ld_scale, typename Store<S>::C *H,
                                                      int average) {
     using C = typename Store<S>::C;
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= v.units) return;
-    AdjUnit un;
-    un.init(u, v);
     // all 19 loads before any store: H and A may alias as far as the
     // compiler knows, so interleaved they made 19 dependent round trips
     C val[Q];
+    if (SP) {
+        if (st.parity == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        val[i] = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
+            for (int i = 0; i < Q; ++i) val[i] = (C)Store<S>::ld(A + (size_t)i * v.units + u, ld_scale);
+        } else {
+            SparseNode sn;
+            sn.init(u, v.sm);
+            val[0] = (C)Store<S>::ld(A + u, ld_scale);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                uint32_t up = sn.up_interior(i);
+                if (cx(i) != 0) up = min(up, v.units - 1u);  // in bounds; x faces redone below
+                const size_t at = (sn.bits & (1u << i)) ? (size_t)i * v.units + u
+                                                        : (size_t)opp(i) * v.units + up;
+                val[i] = (C)Store<S>::ld(A + at, ld_scale);
+            }
+            if (sn.xlo || sn.xhi) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i)
+                    if (cx(i) != 0 && !(sn.bits & (1u << i)))
+                        val[i] = (C)Store<S>::ld(A + (size_t)opp(i) * v.units + sn.up(i, v.sm),
+                                                 ld_scale);
+            }
+        }
+    } else {
+        AdjUnit un;
+        un.init(u, v);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            val[i] = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
+    }
     if (average) {
         C old[Q];
 #pragma unroll
@@ -529,18 +559,31 @@ static void capture(lbm_ctx *c, const AdjView &v, unsigned grid, T *H, int avera
     const AdjState st{c->opt.layout, (int)(c->steps & 1)};
     const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
     const void *A = c->opt.layout == LBM_LAYOUT_AB ? c->d_pop[c->cur] : c->d_pop[0];
+    const bool sp = c->opt.layout == LBM_LAYOUT_SPARSE;
     switch (c->opt.precision) {
     case LBM_FP64:
-        k_adj_capture<double><<<grid, 256, 0, c->stream>>>((const double *)A, v, st, lds,
-                                                           (double *)H, average);
+        if (sp)
+            k_adj_capture<double, true><<<grid, 256, 0, c->stream>>>((const double *)A, v, st, lds,
+                                                                     (double *)H, average);
+        else
+            k_adj_capture<double, false><<<grid, 256, 0, c->stream>>>((const double *)A, v, st, lds,
+                                                                      (double *)H, average);
         break;
     case LBM_FP32_SHIFTED:
-        k_adj_capture<float><<<grid, 256, 0, c->stream>>>((const float *)A, v, st, lds, (float *)H,
-                                                          average);
+        if (sp)
+            k_adj_capture<float, true><<<grid, 256, 0, c->stream>>>((const float *)A, v, st, lds,
+                                                                    (float *)H, average);
+        else
+            k_adj_capture<float, false><<<grid, 256, 0, c->stream>>>((const float *)A, v, st, lds,
+                                                                     (float *)H, average);
         break;
     default:
-        k_adj_capture<__half><<<grid, 256, 0, c->stream>>>((const __half *)A, v, st, lds,
-                                                           (float *)H, average);
+        if (sp)
+            k_adj_capture<__half, true><<<grid, 256, 0, c->stream>>>((const __half *)A, v, st, lds,
+                                                                     (float *)H, average);
+        else
+            k_adj_capture<__half, false><<<grid, 256, 0, c->stream>>>((const __half *)A, v, st, lds,
+                                                                      (float *)H, average);
         break;
     }
     c->launches++;
