@@ -318,6 +318,70 @@ __global__ void __launch_bounds__(256) k_velocity(const S *A, StateView v,
     if (red.partials) block_reduce_velocity<double>(jx, jy, jz, fluid, red);
 }
 
+// Mean-velocity partials alone (no field export), FP32 or FP16 storage: the
+// per-node momentum in float, summed per block as in the stepping kernels.
+// SP: sparse layout, with its streamed values read as the odd step forms
+// them (even parity: the node's own slots; odd parity: the interior
+// upstream formulas, clamped, with the x faces redone).  FP64 arithmetic is
+// scarce on this GPU; the FP64 k_velocity took 9.3 ms at 512^3.
+template <typename S, bool SP>
+__global__ void __launch_bounds__(256) k_velocity_sum(const S *A, StateView v, float Fx, float Fy,
+                                                      float Fz, float ld_scale, Reduce red) {
+    using C = typename Store<S>::C;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    bool fluid = false;
+    C jx = C(0), jy = C(0), jz = C(0);
+    if (u < v.units) {
+        C g[Q];
+        if (SP) {
+            fluid = true;
+            if (v.parity == 0) {
+#pragma unroll
+                for (int j = 1; j < Q; ++j) g[j] = Store<S>::ld(A + (size_t)j * v.units + u, ld_scale);
+            } else {
+                SparseNode sn;
+                sn.init(u, v.sm);
+#pragma unroll
+                for (int j = 1; j < Q; ++j) {
+                    uint32_t up = sn.up_interior(j);
+                    if (cx(j) != 0) up = min(up, v.units - 1u);  // in bounds; x faces redone below
+                    const size_t at = (sn.bits & (1u << j)) ? (size_t)j * v.units + u
+                                                            : (size_t)opp(j) * v.units + up;
+                    g[j] = Store<S>::ld(A + at, ld_scale);
+                }
+                if (sn.xlo || sn.xhi) {
+#pragma unroll
+                    for (int j = 1; j < Q; ++j)
+                        if (cx(j) != 0 && !(sn.bits & (1u << j)))
+                            g[j] = Store<S>::ld(A + (size_t)opp(j) * v.units + sn.up(j, v.sm),
+                                                ld_scale);
+                }
+            }
+        } else {
+            uint32_t node, w;
+            UnitNode nd;
+            fluid = state_unit(v, u, node, w, nd);
+            if (fluid) {
+#pragma unroll
+                for (int j = 1; j < Q; ++j)
+                    g[j] = Store<S>::ld(A + state_loc(v, u, j, 0, w, nd), ld_scale);
+            }
+        }
+        if (fluid) {
+#pragma unroll
+            for (int j = 1; j < Q; ++j) {
+                jx += C(cx(j)) * g[j];
+                jy += C(cy(j)) * g[j];
+                jz += C(cz(j)) * g[j];
+            }
+            jx += C(0.5) * Fx;
+            jy += C(0.5) * Fy;
+            jz += C(0.5) * Fz;
+        }
+    }
+    block_momentum_sum<C>(jx, jy, jz, fluid, red.partials + 3 * (size_t)blockIdx.x, red.flag);
+}
+
 // Export of the post-collision state as unshifted FP64 f[19][N] (dense node
 // order).  Solid nodes are left to the caller (who fills w_i).
 template <typename S>
@@ -527,6 +591,19 @@ int launch_velocity_t(lbm_ctx *c, double *u_dev, bool reduce) {
     if (grid == 0) return 0;
     Reduce red{reduce ? c->d_partials : nullptr, c->d_flag};
     const float lds = c->fp16_scale > 0.f ? 1.0f / c->fp16_scale : 1.0f;
+    if constexpr (sizeof(typename Store<S>::C) == 4) {
+        if (!u_dev && reduce) {
+            const float Fx = (float)c->F[0], Fy = (float)c->F[1], Fz = (float)c->F[2];
+            if (v.layout == LBM_LAYOUT_SPARSE)
+                k_velocity_sum<S, true><<<grid, bs, 0, c->stream>>>((const S *)cur_pop(c), v, Fx, Fy,
+                                                                    Fz, lds, red);
+            else
+                k_velocity_sum<S, false><<<grid, bs, 0, c->stream>>>((const S *)cur_pop(c), v, Fx,
+                                                                     Fy, Fz, lds, red);
+            c->launches++;
+            return (int)grid;
+        }
+    }
     k_velocity<S><<<grid, bs, 0, c->stream>>>((const S *)cur_pop(c), v, c->d_fidx, c->F[0], c->F[1],
                                               c->F[2], lds, u_dev, red);
     c->launches++;
