@@ -271,3 +271,21 @@ def test_512_boolean_sampled_parity(L, ora, geom, layout):
     assert dev_err(got.T, pred.T) <= 1e-5
     nf, _ = S.link_counts()
     assert nf == int((mask == 0).sum())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_mean_velocity_equals_exported_field_mean(L, geom, layout, precision):
+    """lbm_mean_velocity (float momenta, compensated sums for FP32/FP16
+    storage) against the mean of the FP64 velocity-field export, on a ragged
+    lattice with fluid on the x faces, after an odd and an even number of
+    steps."""
+    mask = geom.random_mask((21, 18, 37), 0.3, seed=7)
+    S = L.LBMSolver(mask, "B", 0.8, force=(2e-5, -1e-5, 5e-6), precision=precision, layout=layout)
+    for n in (7, 1):
+        S.step(n)
+        U = S.mean_velocity()
+        u = S.velocity()
+        Uf = np.array([u[a].sum() for a in range(3)]) / mask.size
+        assert np.abs(U - Uf).max() <= 1e-6 * np.abs(Uf).max()
+    S.close()
