@@ -10,6 +10,11 @@
 // implicit device synchronisation.  They pass the populations, the mask and
 // an output slot they already own; this file supplies the scratch.
 //
+// The lattice is read as the periodic, halfway-bounceback problem: any
+// nonzero mask byte is a solid voxel, and a context built with full-way
+// bounceback or bounded faces (pressure drive, symmetry planes) streams
+// differently, so its mean velocity is not this call's.
+//
 // The scratch holds one partial sum per 256-node block, so the lattice is
 // limited to LBM_NOALLOC_MAX_NODES nodes.  Every GPU that loads the library
 // keeps the array (1.5 MiB) until the process exits.  All calls share it and
@@ -128,8 +133,12 @@ extern "C" int lbm_mean_velocity_noalloc(const double *f_dev, const uint8_t *mas
                                          double *U_dev, void *cuda_stream) {
     if (!f_dev || !mask_dev || !dims || !force || !U_dev) return LBM_EINVAL;
     if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return LBM_EINVAL;
+    // each edge alone first, so that the product below cannot overflow
+    const int64_t cap = LBM_NOALLOC_MAX_NODES;
+    if (dims[0] > cap || dims[1] > cap || dims[2] > cap) return LBM_EINVAL;
+    if ((int64_t)dims[0] * dims[1] > cap) return LBM_EINVAL;
     const int64_t N = (int64_t)dims[0] * dims[1] * dims[2];
-    if (N > (int64_t)LBM_NOALLOC_MAX_NODES) return LBM_EINVAL;  // scratch holds N/256 partials
+    if (N > cap) return LBM_EINVAL;  // scratch holds N/256 partials
     double *partials = nullptr;
     int rc = scratch_address(&partials);
     if (rc != LBM_OK) return rc;

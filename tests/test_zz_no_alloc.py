@@ -55,10 +55,35 @@ def test_noalloc_mean_velocity_matches_context(env):
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
-def test_noalloc_rejects_oversized_lattice(env):
+def test_noalloc_mean_velocity_many_blocks(env):
+    """A 100 x 96 x 96 Boolean medium: 3,600 blocks of partials, so the
+    finalising block's strided loop over more than 1,024 partials runs."""
+    torch, lbm, geometry = env
+    lib = lbm.lib()
+    mask = geometry.boolean((100, 96, 96), 5, 0.45, seed=77)[0]
+    F = (2e-6, 1e-6, -1e-6)
+    dims = np.array(mask.shape[::-1], np.int32)
+    S = lbm.LBMSolver(mask, "B", 1.0, force=F, precision="fp64", layout="ab")
+    mask_dev = torch.from_numpy(mask).cuda()
+    U_dev = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    for steps in (7, 12):
+        S.step(steps)
+        f = S.get_populations()
+        g = torch.from_numpy(np.ascontiguousarray(f - W[:, None, None, None])).cuda()
+        got = _call(lib, torch, g, mask_dev, dims, F, U_dev)
+        want = S.mean_velocity()
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    S.close()
+
+
+@pytest.mark.parametrize("dims", [(257, 256, 256), (2**31 - 1, 2**31 - 1, 2**31 - 1),
+                                  (2**31 - 1, 2**20, 1), (1, 1, 2**24 + 1)])
+def test_noalloc_rejects_oversized_lattice(env, dims):
+    """Just over 2^24 nodes, and edges whose product would overflow 64 bits
+    if it were formed before the check."""
     torch, lbm, _ = env
     lib = lbm.lib()
-    dims = np.array([257, 256, 256], np.int32)  # just over 2^24 nodes
+    dims = np.array(dims, np.int32)
     one = torch.zeros(1, dtype=torch.float64, device="cuda")
     m = torch.zeros(1, dtype=torch.uint8, device="cuda")
     rc = lib.lbm_mean_velocity_noalloc(one.data_ptr(), m.data_ptr(), dims,
