@@ -118,6 +118,11 @@ typedef struct {
                                  have one even and one odd value (Sets B, E, SRT;
                                  the same collision as the MRT, fewer operations),
                                  the moment-space MRT otherwise.  1: always MRT. */
+    int32_t index_width;      /* 0 (default) or 32: flat population offsets in 32 bits
+                                 whenever 19 * (stored units) < 2^32, in 64 bits
+                                 beyond; 64: always in 64 bits (the path of very
+                                 large lattices, selectable on small ones for
+                                 testing).  The results are bitwise the same. */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -204,13 +209,18 @@ int lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t count, do
  *   mask_dev device, uint8 [N], 1 = solid
  *   U_dev    device, double[3]: receives the streamed-state mean velocity
  *            (as lbm_mean_velocity: halfway bounceback, F/2 shift, over all N)
+ * The lattice is taken as periodic with halfway bounceback at every nonzero
+ * mask byte: the result equals lbm_mean_velocity only for contexts built
+ * with those boundaries (not with full-way bounceback, pressure faces or
+ * symmetry planes).
  *   cuda_stream  stream to run on (NULL: the legacy default stream)
  * Asynchronous on the stream.  Its scratch is a file-scope device array that
  * every GPU loading the library keeps until exit (1.5 MiB); the first call
  * on a device looks up the array's address (cudaGetSymbolAddress) with that
  * device current, so make that first call before any stream capture.  All
  * calls share the array: calls that overlap on the GPU race.  LBM_EINVAL for
- * a NULL pointer, dims <= 0, or more than LBM_NOALLOC_MAX_NODES nodes. */
+ * a NULL pointer, dims <= 0, or more than LBM_NOALLOC_MAX_NODES nodes (each
+ * edge is checked before the node count is formed). */
 int lbm_mean_velocity_noalloc(const double *f_dev, const uint8_t *mask_dev, const int32_t dims[3],
                               const double force[3], double *U_dev, void *cuda_stream);
 
@@ -223,6 +233,16 @@ int lbm_link_counts(lbm_ctx *ctx, int64_t *n_fluid, int64_t links[19]);
  * solid; direction i at row i-1) and the bounceback bits bbmask[Nf] (bit i
  * set iff x - c_i is solid).  Any pointer may be NULL. */
 int lbm_sparse_tables(lbm_ctx *ctx, int32_t *fluid_idx, int32_t *nbr, uint32_t *bbmask);
+
+/* Reads and clears the context's device flags (synchronises its stream):
+ * bit 0 (1): a measuring launch met a non-finite density or momentum (the
+ * convergence loop reports it as LBM_EUNSTABLE); bit 1 (2): in a library
+ * built with -DLBM_BOUNDS_CHECK, a kernel formed an index outside the array
+ * it was about to access and skipped that access (never set otherwise).
+ * The checked build is a debugging aid for the streaming of eq. (LBE)
+ * over a voxel image (Sec. 2.1): every computed offset into the population,
+ * index-record, row-word and row-start arrays is range-checked first. */
+int lbm_device_flags(lbm_ctx *ctx, int32_t *flags);
 
 /* Number of time steps taken since creation (or since the loaded checkpoint). */
 int64_t lbm_steps_done(const lbm_ctx *ctx);

@@ -38,6 +38,8 @@ struct AdjView {
     const uint32_t *lw;
     SparseMap sm;
     Dims d;
+    // bounds-check build: a location outside the 19 * units slots
+    __device__ __forceinline__ bool ok(size_t at) const { return in_range(at, (uint64_t)Q * units, sm.flag); }
 };
 
 struct AdjUnit {
@@ -215,22 +217,25 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
                 if (cx(i) != 0) up = min(up, v.units - 1u);  // in bounds; x faces redone below
                 const size_t at = (sn.bits & (1u << i)) ? (size_t)i * v.units + u
                                                         : (size_t)opp(i) * v.units + up;
-                val[i] = (C)Store<S>::ld(A + at, ld_scale);
+                val[i] = v.ok(at) ? (C)Store<S>::ld(A + at, ld_scale) : C(0);
             }
             if (sn.xlo || sn.xhi) {
 #pragma unroll
                 for (int i = 1; i < Q; ++i)
-                    if (cx(i) != 0 && !(sn.bits & (1u << i)))
-                        val[i] = (C)Store<S>::ld(A + (size_t)opp(i) * v.units + sn.up(i, v.sm),
-                                                 ld_scale);
+                    if (cx(i) != 0 && !(sn.bits & (1u << i))) {
+                        const size_t at = (size_t)opp(i) * v.units + sn.up(i, v.sm);
+                        val[i] = v.ok(at) ? (C)Store<S>::ld(A + at, ld_scale) : C(0);
+                    }
             }
         }
     } else {
         AdjUnit un;
         un.init(u, v);
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            val[i] = un.fluid ? (C)Store<S>::ld(A + streamed_loc(st, v, u, i, un), ld_scale) : C(0);
+        for (int i = 0; i < Q; ++i) {
+            const size_t at = un.fluid ? streamed_loc(st, v, u, i, un) : 0;
+            val[i] = un.fluid && v.ok(at) ? (C)Store<S>::ld(A + at, ld_scale) : C(0);
+        }
     }
     if (average) {
         C old[Q];
@@ -282,15 +287,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
                 // in bounds; the value is replaced just below
                 uint32_t up = sn.up_interior(o);
                 if (cx(o) != 0) up = min(up, v.units - 1u);
-                phi[i] = (sn.bits & (1u << o)) ? psi_in[(size_t)o * v.units + u]
-                                               : psi_in[(size_t)i * v.units + up];
+                const size_t at = (sn.bits & (1u << o)) ? (size_t)o * v.units + u
+                                                        : (size_t)i * v.units + up;
+                phi[i] = v.ok(at) ? psi_in[at] : T(0);
             }
             if (sn.xlo || sn.xhi) {
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     const int o = opp(i);
-                    if (cx(o) != 0 && !(sn.bits & (1u << o)))
-                        phi[i] = psi_in[(size_t)i * v.units + sn.up(o, v.sm)];
+                    if (cx(o) != 0 && !(sn.bits & (1u << o))) {
+                        const size_t at = (size_t)i * v.units + sn.up(o, v.sm);
+                        phi[i] = v.ok(at) ? psi_in[at] : T(0);
+                    }
                 }
             }
         } else {
@@ -303,8 +311,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     const int o = opp(i);
-                    phi[i] = (w & (1u << o)) ? psi_in[(size_t)o * v.units + u]
-                                             : psi_in[(size_t)i * v.units + dn.up(o)];
+                    const size_t at = (w & (1u << o)) ? (size_t)o * v.units + u
+                                                      : (size_t)i * v.units + dn.up(o);
+                    phi[i] = v.ok(at) ? psi_in[at] : T(0);
                 }
             }
         }
@@ -423,6 +432,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
     // psi_a == psi_b (the transient pass): 0.5 (x + x) is x exactly
     const bool same = psi_a == psi_b;
     auto psi_at = [&](size_t at) -> T {
+        if (!v.ok(at)) return T(0);
         return same ? psi_a[at] : T(0.5) * (psi_a[at] + psi_b[at]);
     };
     if (u < v.units) {

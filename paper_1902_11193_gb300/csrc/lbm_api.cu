@@ -72,6 +72,7 @@ void lbm_default_options(lbm_options *o) {
     o->rho_in = 1.0;
     o->rho_out = 1.0;
     o->collision = 0;
+    o->index_width = 0;
 }
 
 // Table 2 (Sec. 2.3); s_nu = 1/tau in every set.
@@ -172,6 +173,7 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
     if ((o.pressure_x != 0 && o.pressure_x != 1) || o.symmetry < 0 || o.symmetry > 3)
         return LBM_EINVAL;
     if (o.collision != 0 && o.collision != 1) return LBM_EINVAL;
+    if (o.index_width != 0 && o.index_width != 32 && o.index_width != 64) return LBM_EINVAL;
     if ((o.pressure_x || o.symmetry) && (o.layout != LBM_LAYOUT_AB || o.bounceback != 0))
         return LBM_EINVAL;
     if (o.pressure_x && (dims[0] < 2 || force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0 ||
@@ -501,6 +503,16 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
     return rc;
 }
 
+int lbm_device_flags(lbm_ctx *c, int32_t *flags) {
+    if (!c || !flags) return LBM_EINVAL;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *flags = h;
+    return LBM_OK;
+}
+
 int lbm_converged_velocity(lbm_ctx *c, double U[3]) {
     if (!c || !U) return LBM_EINVAL;
     if (!c->has_conv) return LBM_ENOSTATE;
@@ -768,7 +780,7 @@ struct CkptHeader {
 struct CkptDomain {
     int32_t pressure_x, symmetry;
     double rho_in, rho_out;
-    int32_t collision, pad;
+    int32_t collision, index_width;  // index_width: 0 in files written before it existed
 };
 
 int lbm_save(lbm_ctx *c, const char *path) {
@@ -806,7 +818,7 @@ int lbm_save(lbm_ctx *c, const char *path) {
     FILE *fp = fopen(path, "wb");
     if (!fp) return LBM_EIO;
     CkptDomain dm{c->opt.pressure_x, c->opt.symmetry, c->opt.rho_in, c->opt.rho_out,
-                  c->opt.collision, 0};
+                  c->opt.collision, c->opt.index_width};
     bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&dm, sizeof dm, 1, fp) == 1 &&
               fwrite(mask.data(), 1, (size_t)c->N, fp) == (size_t)c->N &&
               (bytes == 0 || fwrite(buf.data(), 1, bytes, fp) == bytes);
@@ -857,6 +869,7 @@ int lbm_load(lbm_ctx **out, const char *path, const lbm_options *opt) {
     o.rho_in = dm.rho_in;
     o.rho_out = dm.rho_out;
     o.collision = dm.collision;
+    o.index_width = dm.index_width;
     lbm_ctx *c = nullptr;
     int rc = lbm_create_rates(&c, mask.data(), h.dims, h.s, h.F, &o);
     if (rc != LBM_OK) {

@@ -153,14 +153,17 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_BATCH_MIN_BLOCKS
                         fl = true;
                         if (odd)
                             aa_sparse_update<S, true, size_t, StoreL2<S>>(
-                                A, L.sm, L.units, u, __ldg(L.sm.nb + u), p, 1.f, 1.f, jx, jy, jz);
+                                A, L.sm, L.units, u, load_chk(L.sm.nb, u, L.units, L.sm.flag), p,
+                                1.f, 1.f, jx, jy, jz);
                         else
                             aa_sparse_update<S, false, size_t, StoreL2<S>>(
                                 A, L.sm, L.units, u, make_uint2(0u, 0u), p, 1.f, 1.f, jx, jy, jz);
                     } else {
                         const uint32_t w = L.lw[u];
-                        fl = odd ? aa_dense_update<S, true, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz)
-                                 : aa_dense_update<S, false, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f, jx, jy, jz);
+                        fl = odd ? aa_dense_update<S, true, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f,
+                                                                        jx, jy, jz, L.sm.flag)
+                                 : aa_dense_update<S, false, StoreL2<S>>(A, u, w, L.d, p, 1.f, 1.f,
+                                                                         jx, jy, jz, L.sm.flag);
                     }
                 }
                 if (slot >= 0)  // the single-lattice block reduction
@@ -294,6 +297,7 @@ BatchLat make_lat(const lbm_ctx *c, int npt) {
     L.pop = c->d_pop[0];
     L.lw = c->d_lw;
     if (c->opt.layout == LBM_LAYOUT_SPARSE) L.sm = sparse_map(c);
+    L.sm.flag = c->d_flag;  // the member's own flag (bounds-check build)
     L.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
     L.pf = make_collide<float>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);
     L.pd = make_collide<double>(c->s, c->F, c->opt.linear_eq, c->opt.collision == 0);

@@ -43,7 +43,8 @@ struct Domain {
 template <typename S>
 __device__ __forceinline__ void bounded_pull(const S *__restrict__ A, const uint8_t *__restrict__ mask,
                                              const Dims &d, const Domain &dom, int x, int y, int z,
-                                             uint32_t n, float lds, typename Store<S>::C g[Q]) {
+                                             uint32_t n, float lds, typename Store<S>::C g[Q],
+                                             int *flag) {
     using C = typename Store<S>::C;
     uint32_t unknown = 0;
 #pragma unroll
@@ -70,8 +71,9 @@ __device__ __forceinline__ void bounded_pull(const S *__restrict__ A, const uint
         }
         const int dir = my ? (mz ? mirror_z(mirror_y(j)) : mirror_y(j)) : (mz ? mirror_z(j) : j);
         const uint32_t s = (uint32_t)xs + (uint32_t)d.Lx * ((uint32_t)ys + (uint32_t)d.Ly * (uint32_t)zs);
-        g[j] = mask[s] ? Store<S>::ld(A + (size_t)opp(j) * d.N + n, lds)
-                       : Store<S>::ld(A + (size_t)dir * d.N + s, lds);
+        const bool solid = in_range(s, d.N, flag) ? mask[s] != 0 : true;
+        const size_t at = solid ? (size_t)opp(j) * d.N + n : (size_t)dir * d.N + s;
+        g[j] = in_range(at, (uint64_t)Q * d.N, flag) ? Store<S>::ld(A + at, lds) : C(0);
     }
     if (unknown) {
         const int nx = x == 0 ? 1 : -1;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(256) k_ab_bounded(const S *__restrict__ src, S
         int x, y, z;
         node_xyz(n, d, x, y, z);
         C g[Q];
-        bounded_pull<S>(src, mask, d, dom, x, y, z, n, lds, g);
+        bounded_pull<S>(src, mask, d, dom, x, y, z, n, lds, g, flag);
         collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * d.N + n, g[i], sts);
@@ -151,7 +153,8 @@ template <typename S>
 __global__ void __launch_bounds__(256) k_velocity_bounded(const S *__restrict__ A,
                                                           const uint8_t *__restrict__ mask, Dims d,
                                                           Domain dom, double Fx, double Fy, double Fz,
-                                                          float lds, double *u_out, double *partials) {
+                                                          float lds, double *u_out, double *partials,
+                                                          int *flag) {
     using C = typename Store<S>::C;
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool fluid = n < d.N && !mask[n];
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(256) k_velocity_bounded(const S *__restrict__ 
         int x, y, z;
         node_xyz(n, d, x, y, z);
         C g[Q];
-        bounded_pull<S>(A, mask, d, dom, x, y, z, n, lds, g);
+        bounded_pull<S>(A, mask, d, dom, x, y, z, n, lds, g, flag);
 #pragma unroll
         for (int j = 1; j < Q; ++j) {
             v[0] += cx(j) * (double)g[j];
@@ -210,7 +213,8 @@ int velocity_bounded_t(lbm_ctx *c, double *u_dev, bool reduce) {
     const unsigned grid = (unsigned)((c->N + 255) / 256);
     k_velocity_bounded<S><<<grid, 256, 0, c->stream>>>((const S *)c->d_pop[c->cur], c->d_mask, d,
                                                        domain_of(c), c->F[0], c->F[1], c->F[2], lds,
-                                                       u_dev, reduce ? c->d_partials : nullptr);
+                                                       u_dev, reduce ? c->d_partials : nullptr,
+                                                       c->d_flag);
     c->launches++;
     return (int)grid;
 }

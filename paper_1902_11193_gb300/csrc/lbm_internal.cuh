@@ -140,7 +140,35 @@ struct SparseMap {
     const int32_t *rstart;
     int Lx, Ly, Lz, Wr;
     uint64_t mLx, mLy;
+    int *flag;  // the context's device flag (bounds-check build: FLAG_BOUNDS)
 };
+
+// Bits of a context's device flag.
+constexpr int FLAG_NONFINITE = 1;  // a non-finite density or momentum
+constexpr int FLAG_BOUNDS = 2;     // an index out of range (bounds-check build)
+
+// Bounds-check build (-DLBM_BOUNDS_CHECK): every computed offset into the
+// population, index-record, row-word and row-start arrays is range-checked
+// before the access; an offset out of range skips the access and raises
+// FLAG_BOUNDS in the context's flag, which lbm_device_flags reports.  It
+// never traps, so the context stays usable.  In the normal build in_range
+// is the constant true and compiles away.
+#ifdef LBM_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+__device__ __forceinline__ bool in_range(uint64_t i, uint64_t n, int *flag) {
+    if (!kBoundsCheck) return true;
+    if (i < n) return true;
+    if (flag) atomicOr(flag, FLAG_BOUNDS);
+    return false;
+}
+// p[i], or 0 where i >= n (bounds-check build only; plain p[i] otherwise).
+template <typename T>
+__device__ __forceinline__ T load_chk(const T *p, uint64_t i, uint64_t n, int *flag) {
+    return in_range(i, n, flag) ? p[i] : T{};
+}
 
 __host__ __forceinline__ uint64_t div_magic(uint32_t L) {
     // ceil(2^64 / L) for L >= 2; L == 1 is handled by the caller

@@ -50,15 +50,14 @@ __global__ void __launch_bounds__(256) k_ab(const S *__restrict__ src, S *__rest
     if (fluid || (w & BBNODE_BIT)) {
         DenseNode nd;
         nd.init(n, d);
+        const uint64_t lim = (uint64_t)Q * d.N;
         C g[Q];
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
-            if (j == 0)
-                g[j] = Store<S>::ld(src + n, ld_scale);
-            else if (w & (1u << j))
-                g[j] = Store<S>::ld(src + (size_t)opp(j) * d.N + n, ld_scale);
-            else
-                g[j] = Store<S>::ld(src + (size_t)j * d.N + nd.up(j), ld_scale);
+            const size_t at = j == 0 ? (size_t)n
+                              : (w & (1u << j)) ? (size_t)opp(j) * d.N + n
+                                                : (size_t)j * d.N + nd.up(j);
+            g[j] = in_range(at, lim, red.flag) ? Store<S>::ld(src + at, ld_scale) : C(0);
         }
         if (fluid) {
             collide_as<K, C>(g, p, jx, jy, jz);
@@ -84,7 +83,8 @@ __global__ void __launch_bounds__(256) k_aa(S *A, const uint32_t *__restrict__ l
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t w = n < d.N ? lw[n] : SOLID_BIT;
     C jx = C(0), jy = C(0), jz = C(0);
-    const bool fluid = aa_dense_update<S, ODD, Store<S>, K>(A, n, w, d, p, ld_scale, st_scale, jx, jy, jz);
+    const bool fluid = aa_dense_update<S, ODD, Store<S>, K>(A, n, w, d, p, ld_scale, st_scale, jx,
+                                                            jy, jz, red.flag);
     if (red.partials) block_reduce_velocity<C>(jx, jy, jz, fluid, red);
 }
 
@@ -238,6 +238,8 @@ struct StateView {
     const uint32_t *lw;
     SparseMap sm;
     Dims d;
+    // bounds-check build: a location outside the 19 * units slots
+    __device__ __forceinline__ bool ok(size_t at) const { return in_range(at, (uint64_t)Q * units, sm.flag); }
 };
 
 struct UnitNode {
@@ -298,7 +300,8 @@ __global__ void __launch_bounds__(256) k_velocity(const S *A, StateView v,
         if (fluid) {
 #pragma unroll
             for (int j = 1; j < Q; ++j) {
-                double gj = (double)Store<S>::ld(A + state_loc(v, u, j, 0, w, nd), ld_scale);
+                const size_t at = state_loc(v, u, j, 0, w, nd);
+                double gj = v.ok(at) ? (double)Store<S>::ld(A + at, ld_scale) : 0.0;
                 jx += cx(j) * gj;
                 jy += cy(j) * gj;
                 jz += cz(j) * gj;
@@ -347,14 +350,15 @@ __global__ void __launch_bounds__(256) k_velocity_sum(const S *A, StateView v, f
                     if (cx(j) != 0) up = min(up, v.units - 1u);  // in bounds; x faces redone below
                     const size_t at = (sn.bits & (1u << j)) ? (size_t)j * v.units + u
                                                             : (size_t)opp(j) * v.units + up;
-                    g[j] = Store<S>::ld(A + at, ld_scale);
+                    g[j] = v.ok(at) ? Store<S>::ld(A + at, ld_scale) : C(0);
                 }
                 if (sn.xlo || sn.xhi) {
 #pragma unroll
                     for (int j = 1; j < Q; ++j)
-                        if (cx(j) != 0 && !(sn.bits & (1u << j)))
-                            g[j] = Store<S>::ld(A + (size_t)opp(j) * v.units + sn.up(j, v.sm),
-                                                ld_scale);
+                        if (cx(j) != 0 && !(sn.bits & (1u << j))) {
+                            const size_t at = (size_t)opp(j) * v.units + sn.up(j, v.sm);
+                            g[j] = v.ok(at) ? Store<S>::ld(A + at, ld_scale) : C(0);
+                        }
                 }
             }
         } else {
@@ -363,8 +367,10 @@ __global__ void __launch_bounds__(256) k_velocity_sum(const S *A, StateView v, f
             fluid = state_unit(v, u, node, w, nd);
             if (fluid) {
 #pragma unroll
-                for (int j = 1; j < Q; ++j)
-                    g[j] = Store<S>::ld(A + state_loc(v, u, j, 0, w, nd), ld_scale);
+                for (int j = 1; j < Q; ++j) {
+                    const size_t at = state_loc(v, u, j, 0, w, nd);
+                    g[j] = v.ok(at) ? Store<S>::ld(A + at, ld_scale) : C(0);
+                }
             }
         }
         if (fluid) {
@@ -396,7 +402,8 @@ __global__ void __launch_bounds__(256) k_export(const S *A, StateView v,
     const size_t out = v.layout == LBM_LAYOUT_SPARSE ? (size_t)fidx[u] : (size_t)u;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        double gv = (double)Store<S>::ld(A + state_loc(v, u, j, 1, w, nd), ld_scale);
+        const size_t at = state_loc(v, u, j, 1, w, nd);
+        double gv = v.ok(at) ? (double)Store<S>::ld(A + at, ld_scale) : 0.0;
         f[(size_t)opp(j) * v.d.N + out] = gv + weight(opp(j));
     }
 }
@@ -413,7 +420,8 @@ __global__ void __launch_bounds__(256) k_import(S *A, StateView v, const int32_t
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         double fv = f[(size_t)opp(j) * v.d.N + in] - weight(opp(j));
-        Store<S>::st(A + state_loc(v, u, j, 1, w, nd), (typename Store<S>::C)fv, st_scale);
+        const size_t at = state_loc(v, u, j, 1, w, nd);
+        if (v.ok(at)) Store<S>::st(A + at, (typename Store<S>::C)fv, st_scale);
     }
 }
 
@@ -457,7 +465,10 @@ __global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         double val = weight(opp(j));
-        if (fluid) val += (double)Store<S>::ld(A + state_loc(v, unit, j, 1, w, nd), ld_scale);
+        if (fluid) {
+            const size_t at = state_loc(v, unit, j, 1, w, nd);
+            if (v.ok(at)) val += (double)Store<S>::ld(A + at, ld_scale);
+        }
         f[(size_t)k * Q + opp(j)] = val;
     }
 }
@@ -465,6 +476,12 @@ __global__ void __launch_bounds__(256) k_export_at(const S *A, StateView v,
 // ---------------------------------------------------------------- launchers
 
 static inline unsigned nblocks(uint64_t units, int bs) { return (unsigned)((units + bs - 1) / bs); }
+
+// 32-bit population offsets: whenever 19 * Nf < 2^32, unless the context
+// asked for 64-bit offsets (lbm_options.index_width = 64).
+static inline bool narrow_index(const lbm_ctx *c) {
+    return c->opt.index_width != 64 && 19 * (uint64_t)c->Nf < (uint64_t(1) << 32);
+}
 
 SparseMap sparse_map(const lbm_ctx *c) {
     SparseMap m;
@@ -479,6 +496,7 @@ SparseMap sparse_map(const lbm_ctx *c) {
     m.Wr = c->Wr;
     m.mLx = div_magic((uint32_t)c->Lx);
     m.mLy = div_magic((uint32_t)c->Ly);
+    m.flag = c->d_flag;
     return m;
 }
 
@@ -511,7 +529,7 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
         // measuring steps write one partial per 256 fluid nodes
         const unsigned groups = (unsigned)((c->Nf + 255) / 256);
         if constexpr (sizeof(S) <= 4) {
-            if (!odd && 19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+            if (!odd && narrow_index(c)) {
                 const unsigned g2 = (unsigned)((c->Nf + 511) / 512);
                 if (reduce)
                     k_sparse_even_x2<S, K, true><<<g2, 256, 0, c->stream>>>(
@@ -529,7 +547,7 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
             const SparseMap sm = sparse_map(c);
             S *A = (S *)c->d_pop[0];
             const uint32_t Nf = (uint32_t)c->Nf;
-            if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {
+            if (narrow_index(c)) {
                 if (reduce)
                     k_sparse_odd_t<S, uint32_t, LBM_SPARSE_ODD_NPT, K, true>
                         <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
@@ -545,7 +563,7 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
                         <<<tg, 256, 0, c->stream>>>(A, sm, Nf, p, lds, sts, red);
             }
             grid = reduce ? groups : tg;
-        } else if (19 * (uint64_t)c->Nf < (uint64_t(1) << 32)) {  // even steps, FP64 storage
+        } else if (narrow_index(c)) {  // even steps, FP64 storage
             k_sparse<S, false, uint32_t, K><<<grid, bs, 0, c->stream>>>(
                 (S *)c->d_pop[0], sparse_map(c), (uint32_t)c->Nf, p, lds, sts, red);
         } else {

@@ -63,6 +63,12 @@ __global__ void __launch_bounds__(kThreads) k_velocity_static(const double *__re
             ys = ys < 0 ? ys + Ly : (ys >= Ly ? ys - Ly : ys);
             zs = zs < 0 ? zs + Lz : (zs >= Lz ? zs - Lz : zs);
             const uint32_t up = (uint32_t)xs + (uint32_t)Lx * ((uint32_t)ys + (uint32_t)Ly * (uint32_t)zs);
+            // bounds-check build: an index out of range makes the result NaN
+            // (this call has no context whose flag could carry it)
+            if (kBoundsCheck && up >= N) {
+                v[0] = v[1] = v[2] = NAN;
+                break;
+            }
             const double gi = mask[up] ? g[(size_t)opp(i) * N + n] : g[(size_t)i * N + up];
             v[0] += cx(i) * gi;
             v[1] += cy(i) * gi;

@@ -61,6 +61,16 @@ struct SparseNode {
         init_from(kk, v.x, v.y, m);
     }
 
+    // One row word and one row-start entry (bounds-check build: range-checked).
+    __device__ __forceinline__ uint2 row_word(const SparseMap &m, uint32_t at) const {
+        if (!in_range(at, (uint64_t)m.Ly * m.Lz * m.Wr, m.flag)) return make_uint2(0u, 0u);
+        return __ldg(reinterpret_cast<const uint2 *>(m.rw) + at);
+    }
+    __device__ __forceinline__ int32_t row_start(const SparseMap &m, uint32_t at) const {
+        if (!in_range(at, (uint64_t)m.Ly * m.Lz + 1, m.flag)) return 0;
+        return __ldg(m.rstart + at);
+    }
+
     // n: node index of fluid node kk, b: its bounceback bits
     __device__ __forceinline__ void init_from(uint32_t kk, uint32_t n, uint32_t b,
                                               const SparseMap &m) {
@@ -85,7 +95,7 @@ struct SparseNode {
         // than branching on the bounceback bits
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            const uint2 rw = __ldg(reinterpret_cast<const uint2 *>(m.rw) + (yo[1 + slot_dy(s)] + zo[1 + slot_dz(s)] + w));
+            const uint2 rw = row_word(m, yo[1 + slot_dy(s)] + zo[1 + slot_dz(s)] + w);
             rank[s] = (int32_t)rw.y + __popc(rw.x & below);
         }
     }
@@ -116,20 +126,20 @@ struct SparseNode {
         const int dx = cx(j);
         if (cy(j) == 0 && cz(j) == 0) {  // own row
             if (dx > 0) {
-                if (xlo) return (uint32_t)(__ldg(m.rstart + ((uint32_t)y + (uint32_t)m.Ly * z + 1)) - 1);
+                if (xlo) return (uint32_t)(row_start(m, (uint32_t)y + (uint32_t)m.Ly * z + 1) - 1);
                 return k - 1;
             }
-            if (xhi) return (uint32_t)__ldg(m.rstart + ((uint32_t)y + (uint32_t)m.Ly * z));
+            if (xhi) return (uint32_t)row_start(m, (uint32_t)y + (uint32_t)m.Ly * z);
             return k + 1;
         }
         const int s = row_slot(j);
         if (dx == 0) return (uint32_t)rank[s];
         if (dx > 0) {  // upstream at x - 1
-            if (xlo) return (uint32_t)(__ldg(m.rstart + (nrow(m, s) + 1)) - 1);
+            if (xlo) return (uint32_t)(row_start(m, nrow(m, s) + 1) - 1);
             return (uint32_t)(rank[s] - 1);
         }
         // upstream at x + 1: skip (x, row) if that voxel is fluid
-        if (xhi) return (uint32_t)__ldg(m.rstart + (nrow(m, s)));
+        if (xhi) return (uint32_t)row_start(m, nrow(m, s));
         return (uint32_t)rank[s] + ((bits >> slot_axis_dir(s)) & 1u ? 0u : 1u);
     }
 };

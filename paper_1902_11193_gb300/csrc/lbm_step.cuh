@@ -142,19 +142,79 @@ __device__ __forceinline__ bool aa_dense_update(S *A, uint32_t n, uint32_t w, co
                                                 const Collide<typename Store<S>::C> &p,
                                                 float ld_scale, float st_scale,
                                                 typename Store<S>::C &jx, typename Store<S>::C &jy,
-                                                typename Store<S>::C &jz) {
+                                                typename Store<S>::C &jz, int *flag = nullptr) {
     using C = typename Store<S>::C;
     if (w & SOLID_BIT) return false;
     DenseNode nd;
     if (ODD) nd.init(n, d);
+    const uint64_t lim = (uint64_t)Q * d.N;
     C g[Q];
 #pragma unroll
-    for (int j = 0; j < Q; ++j) g[j] = Acc::ld(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), ld_scale);
+    for (int j = 0; j < Q; ++j) {
+        const size_t at = aa_loc_dense<ODD>(j, n, w, nd, d.N);
+        g[j] = in_range(at, lim, flag) ? Acc::ld(A + at, ld_scale) : C(0);
+    }
+    collide_as<K, C>(g, p, jx, jy, jz);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const size_t at = aa_loc_dense<ODD>(j, n, w, nd, d.N);
+        if (in_range(at, lim, flag)) Acc::st(A + at, g[opp(j)], st_scale);
+    }
+    return true;
+}
+
+// Locations (flat offsets into the population array) that an odd AA step
+// of the sparse layout reads and writes for fluid node k, whose
+// {node index, bounceback bits} record is `nb`: slot opp(j) of the upstream
+// fluid node x - c_j, or slot j of k itself where that voxel is solid
+// (halfway bounceback); loc[0] = k.
+// Interior formulas for every node, then the periodic wrap in x for the few
+// nodes on the x faces; measured faster than one path that tests for the
+// wrap in every direction.
+template <typename Idx>
+__device__ __forceinline__ void odd_locations_of(const SparseNode &sn, const SparseMap &m,
+                                                 uint32_t Nf, Idx loc[Q]) {
+    const uint32_t k = sn.k;
+    loc[0] = k;
+#pragma unroll
+    for (int j = 1; j < Q; ++j)
+        loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k : (Idx)opp(j) * Nf + sn.up_interior(j);
+    if (sn.xlo || sn.xhi) {
+#pragma unroll
+        for (int j = 1; j < Q; ++j)
+            if (cx(j) != 0 && !(sn.bits & (1u << j))) loc[j] = (Idx)opp(j) * Nf + sn.up(j, m);
+    }
+}
+
+template <typename Idx>
+__device__ __forceinline__ void odd_sparse_locations(const SparseMap &m, uint32_t Nf, uint32_t k,
+                                                     uint2 nb, Idx loc[Q]) {
+    SparseNode sn;
+    sn.init_from(k, nb.x, nb.y, m);
+    odd_locations_of<Idx>(sn, m, Nf, loc);
+}
+
+// Gathers the 19 populations of one fluid node from `loc`, collides them
+// and stores the post-collision values of the opposite directions back to
+// the same locations (the AA pattern).
+template <typename S, typename Idx, typename Acc = Store<S>, int K = kCollideRuntime>
+__device__ __forceinline__ void aa_sparse_update_at(S *A, const SparseMap &m, uint32_t Nf,
+                                                    const Idx loc[Q],
+                                                    const Collide<typename Store<S>::C> &p,
+                                                    float ld_scale, float st_scale,
+                                                    typename Store<S>::C &jx,
+                                                    typename Store<S>::C &jy,
+                                                    typename Store<S>::C &jz) {
+    using C = typename Store<S>::C;
+    const uint64_t lim = (uint64_t)Q * Nf;
+    C g[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+        g[j] = in_range(loc[j], lim, m.flag) ? Acc::ld(A + loc[j], ld_scale) : C(0);
     collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
     for (int j = 0; j < Q; ++j)
-        Acc::st(A + aa_loc_dense<ODD>(j, n, w, nd, d.N), g[opp(j)], st_scale);
-    return true;
+        if (in_range(loc[j], lim, m.flag)) Acc::st(A + loc[j], g[opp(j)], st_scale);
 }
 
 // Sparse AA update of fluid node k; an odd step takes the node's
@@ -166,34 +226,14 @@ __device__ __forceinline__ void aa_sparse_update(S *A, const SparseMap &m, uint3
                                                  typename Store<S>::C &jx,
                                                  typename Store<S>::C &jy,
                                                  typename Store<S>::C &jz) {
-    using C = typename Store<S>::C;
     Idx loc[Q];
     if (ODD) {
-        SparseNode sn;
-        sn.init_from(k, nb.x, nb.y, m);
-        loc[0] = k;
-        // Interior formulas for every node, then the periodic wrap in x for
-        // the few nodes on the x faces; measured faster than one path that
-        // tests for the wrap in every direction.
-#pragma unroll
-        for (int j = 1; j < Q; ++j)
-            loc[j] = (sn.bits & (1u << j)) ? (Idx)j * Nf + k
-                                            : (Idx)opp(j) * Nf + sn.up_interior(j);
-        if (sn.xlo || sn.xhi) {
-#pragma unroll
-            for (int j = 1; j < Q; ++j)
-                if (cx(j) != 0 && !(sn.bits & (1u << j))) loc[j] = (Idx)opp(j) * Nf + sn.up(j, m);
-        }
+        odd_sparse_locations<Idx>(m, Nf, k, nb, loc);
     } else {
 #pragma unroll
         for (int j = 0; j < Q; ++j) loc[j] = (Idx)j * Nf + k;
     }
-    C g[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) g[j] = Acc::ld(A + loc[j], ld_scale);
-    collide_as<K, C>(g, p, jx, jy, jz);
-#pragma unroll
-    for (int j = 0; j < Q; ++j) Acc::st(A + loc[j], g[opp(j)], st_scale);
+    aa_sparse_update_at<S, Idx, Acc, K>(A, m, Nf, loc, p, ld_scale, st_scale, jx, jy, jz);
 }
 
 }  // namespace lbm

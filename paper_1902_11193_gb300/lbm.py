@@ -64,7 +64,8 @@ class Options(C.Structure):
                 ("fp16_scale_log2", C.c_int32), ("block_size", C.c_int32),
                 ("stop_rule", C.c_int32), ("bounceback", C.c_int32),
                 ("pressure_x", C.c_int32), ("symmetry", C.c_int32),
-                ("rho_in", C.c_double), ("rho_out", C.c_double), ("collision", C.c_int32)]
+                ("rho_in", C.c_double), ("rho_out", C.c_double), ("collision", C.c_int32),
+                ("index_width", C.c_int32)]
 
 
 _lib = None
@@ -107,6 +108,7 @@ def lib():
             "lbm_adjoint_transient": (C.c_int, [vp, i64, C.POINTER(Grad)]),
             "lbm_mean_velocity_noalloc": (C.c_int, [vp, vp, i32p, dp, vp, vp]),
             "lbm_converged_velocity": (C.c_int, [vp, dp]),
+            "lbm_device_flags": (C.c_int, [vp, C.POINTER(i32)]),
             "lbm_converged_permeability": (C.c_int, [vp, dp]),
             "lbm_batch_default_options": (None, [C.POINTER(BatchOptions)]),
             "lbm_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(LatticeDesc),
@@ -159,13 +161,15 @@ class LBMSolver:
     density boundaries (force must be 0); symmetry: "y", "z" or "yz" makes
     those faces mirror planes (AB layout, halfway bounceback).  collision:
     "auto" (link-basis TRT where the rates allow, MRT otherwise) or "mrt".
+    index_width: 0 (automatic) or 64 (64-bit population offsets even where
+    32 bits would do; the path of very large lattices, bitwise the same).
     """
 
     def __init__(self, mask, set_="B", tau=1.0, Lambda=3.0 / 16.0, force=(1e-6, 0.0, 0.0), *,
                  rates_=None, precision="fp32", layout="aa", check_interval=100,
                  linear_eq=False, max_steps=1_000_000, stream=None, fp16_scale_log2=0,
                  block_size=0, stop_rule=0, bounceback="halfway", pressure=None, symmetry="",
-                 collision="auto"):
+                 collision="auto", index_width=0):
         self.mask = np.ascontiguousarray(mask, np.uint8)
         if self.mask.ndim != 3:
             raise ValueError("mask must be [Lz, Ly, Lx]")
@@ -188,6 +192,7 @@ class LBMSolver:
             o.rho_in, o.rho_out = (float(v) for v in pressure)
         o.symmetry = (1 if "y" in symmetry else 0) | (2 if "z" in symmetry else 0)
         o.collision = {"auto": 0, "mrt": 1}[collision]
+        o.index_width = int(index_width)
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self.options = o
@@ -264,6 +269,14 @@ class LBMSolver:
         k = np.zeros(3)
         _check(lib().lbm_permeability(self._h, k), "lbm_permeability")
         return k
+
+    def device_flags(self) -> int:
+        """Reads and clears the device flags (lbm_device_flags): 1 = a
+        non-finite value was measured, 2 = an index out of range was skipped
+        (bounds-check build only)."""
+        f = C.c_int32(0)
+        _check(lib().lbm_device_flags(self._h, C.byref(f)), "lbm_device_flags")
+        return int(f.value)
 
     def converged_velocity(self) -> np.ndarray:
         """The mean velocity the last stopping-rule run stopped on."""
