@@ -119,6 +119,9 @@ static void free_ctx(lbm_ctx *c) {
     cudaFree(c->d_nb);
     cudaFree(c->d_rw);
     cudaFree(c->d_rstart);
+    cudaFree(c->d_orec);
+    cudaFree(c->d_rwp);
+    cudaFree(c->d_rse);
     cudaFree(c->d_pop[0]);
     cudaFree(c->d_pop[1]);
     cudaFree(c->d_partials);
@@ -245,6 +248,12 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
         const size_t nrows = (size_t)c->Ly * c->Lz;
         CKF(cudaMalloc(&c->d_rw, sizeof(RowWord) * nrows * c->Wr));
         CKF(cudaMalloc(&c->d_rstart, sizeof(int32_t) * (nrows + 1)));
+        if (Nf > 0 && (uint32_t)c->Lx < kOddMaxLx) {
+            const size_t prows = (size_t)(c->Ly + 2) * (size_t)(c->Lz + 2);
+            CKF(cudaMalloc(&c->d_orec, sizeof(uint2) * (size_t)Nf));
+            CKF(cudaMalloc(&c->d_rwp, sizeof(RowWord) * prows * c->Wr));
+            CKF(cudaMalloc(&c->d_rse, sizeof(int2) * prows));
+        }
         rc = build_sparse_links(c, d_links);
     } else {
         CKF(cudaMalloc(&c->d_lw, sizeof(uint32_t) * (size_t)N));

@@ -42,6 +42,9 @@ struct lbm_ctx {
     uint2 *d_nb;          // [Nf] sparse: {node index, bounceback bits} interleaved
     lbm::RowWord *d_rw;   // [Ly*Lz][Wr] sparse: row fluid bits + fluid index base
     int32_t *d_rstart;    // [Ly*Lz + 1] sparse: fluid index of each row's first node
+    uint2 *d_orec;        // [Nf] sparse, Lx < 2^13: {padded row, bits | x << 19} (OddMap)
+    lbm::RowWord *d_rwp;  // [(Ly+2)*(Lz+2)][Wr] padded row words (OddMap)
+    int2 *d_rse;          // [(Ly+2)*(Lz+2)] padded row start/end (OddMap)
     int Wr;               // 32-voxel words per row
     void *d_pop[2];       // populations; AB uses both, AA and SPARSE one
     size_t elem;          // bytes per stored population value

@@ -170,6 +170,34 @@ __device__ __forceinline__ T load_chk(const T *p, uint64_t i, uint64_t n, int *f
     return in_range(i, n, flag) ? p[i] : T{};
 }
 
+// The odd AA step of the sparse layout with its index arithmetic cut down
+// (k_sparse_odd_l).  Set up once per context:
+//  rec[k]  {padded row p, bounceback bits | x << 19} of fluid node k, where
+//          p = (y + 1) + (Ly + 2)(z + 1) numbers the rows of the lattice
+//          padded by one ghost row on each side in y and z (needs Lx < 2^13);
+//  rwp     the row words (RowWord) of the padded rows, Wr per row, the ghost
+//          rows copies of the rows they stand for (periodic in y and z);
+//  rse     per padded row {fluid index of the row's first fluid voxel, one
+//          past its last}.
+// Neighbour row slot s of padded row p is p + dy_s + (Ly + 2) dz_s, so each
+// slot's base pointer is offset once on the host (rws, rse) and a node's
+// row word w of slot s is rws[s][p Wr + w]: no division, no wrap test.
+// slot[j] = j Nf puts the slot offsets in the kernel's parameter bank.
+struct OddMap {
+    const uint2 *rec;
+    const RowWord *rws[8];  // rwp shifted to neighbour row slot s
+    const int2 *rse[9];     // rse shifted to slot s; [8]: the own row
+    uint32_t slot[19];      // j * Nf
+    uint32_t Wr, Lx;
+    // bounds-check build: the unshifted tables and their sizes
+    const RowWord *rwp;
+    const int2 *rse0;
+    int32_t roff[9];        // row offset of each slot (0 for the own row)
+    uint32_t nprows;        // padded rows
+    int *flag;
+};
+constexpr uint32_t kOddMaxLx = 1u << 13;  // x must fit 13 bits of the record
+
 __host__ __forceinline__ uint64_t div_magic(uint32_t L) {
     // ceil(2^64 / L) for L >= 2; L == 1 is handled by the caller
     return L <= 1 ? 0 : (~uint64_t(0)) / L + 1;

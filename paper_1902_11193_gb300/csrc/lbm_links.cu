@@ -203,6 +203,32 @@ __global__ void k_sparse_links(const int32_t *__restrict__ fidx, uint32_t Nf, in
     count_links(bits, valid, links);
 }
 
+// Padded row tables of OddMap: row words and {row start, row end} of the
+// lattice padded by one ghost row on each side in y and z.
+__global__ void k_pad_rows(const RowWord *__restrict__ rw, const int32_t *__restrict__ rstart,
+                           int Ly, int Lz, int Wr, uint32_t nwords, RowWord *rwp, int2 *rse) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nwords) return;
+    const uint32_t p = t / (uint32_t)Wr, w = t - p * (uint32_t)Wr;
+    const int yp = (int)(p % (uint32_t)(Ly + 2)), zp = (int)(p / (uint32_t)(Ly + 2));
+    const int y = yp == 0 ? Ly - 1 : (yp == Ly + 1 ? 0 : yp - 1);
+    const int z = zp == 0 ? Lz - 1 : (zp == Lz + 1 ? 0 : zp - 1);
+    const uint32_t R = (uint32_t)y + (uint32_t)Ly * (uint32_t)z;
+    rwp[t] = rw[(size_t)R * Wr + w];
+    if (w == 0) rse[p] = make_int2(rstart[R], rstart[R + 1]);
+}
+
+// OddMap record of every fluid node: {padded row, bounceback bits | x << 19}.
+__global__ void k_odd_records(const uint2 *__restrict__ nb, uint32_t Nf, int Lx, int Ly,
+                              uint2 *orec) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nf) return;
+    const uint2 v = nb[k];
+    const uint32_t R = v.x / (uint32_t)Lx, x = v.x - R * (uint32_t)Lx;
+    const uint32_t z = R / (uint32_t)Ly, y = R - z * (uint32_t)Ly;
+    orec[k] = make_uint2((y + 1u) + (uint32_t)(Ly + 2) * (z + 1u), v.y | (x << 19));
+}
+
 // ---------------------------------------------------------------- launchers
 
 int build_dense_links(lbm_ctx *c, unsigned long long *d_links) {
@@ -233,6 +259,14 @@ int build_sparse_links(lbm_ctx *c, unsigned long long *d_links) {
         k_sparse_links<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_fidx, Nf, c->Lx, c->Ly, c->Lz,
                                                                  c->d_mask, c->d_bb, c->d_nb, d_links);
     c->launches += 5;
+    if (c->d_orec) {
+        const uint32_t pw = (uint32_t)(c->Ly + 2) * (uint32_t)(c->Lz + 2) * (uint32_t)c->Wr;
+        k_pad_rows<<<(pw + 255) / 256, 256, 0, c->stream>>>(c->d_rw, c->d_rstart, c->Ly, c->Lz,
+                                                            c->Wr, pw, c->d_rwp, c->d_rse);
+        k_odd_records<<<(Nf + 255) / 256, 256, 0, c->stream>>>(c->d_nb, Nf, c->Lx, c->Ly,
+                                                               c->d_orec);
+        c->launches += 2;
+    }
     uint32_t tot = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);

@@ -194,6 +194,59 @@ __device__ __forceinline__ void odd_sparse_locations(const SparseMap &m, uint32_
     odd_locations_of<Idx>(sn, m, Nf, loc);
 }
 
+// odd_sparse_locations from an OddMap record: the same locations, bit for
+// bit, with less index arithmetic (see OddMap).
+__device__ __forceinline__ void odd_lean_locations(const OddMap &o, uint32_t k, uint2 rec,
+                                                   uint32_t loc[Q]) {
+    const uint32_t p = rec.x, bits = rec.y & 0x7FFFEu, x = rec.y >> 19;
+    const uint32_t e = p * o.Wr + (x >> 5);
+    const uint32_t below = (1u << (x & 31u)) - 1u;
+    int32_t rank[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        uint2 v = make_uint2(0u, 0u);
+        if (!kBoundsCheck || in_range((uint64_t)((int64_t)e + (int64_t)o.roff[s] * o.Wr),
+                                      (uint64_t)o.nprows * o.Wr, o.flag))
+            v = __ldg(reinterpret_cast<const uint2 *>(o.rws[s]) + e);
+        rank[s] = (int32_t)v.y + __popc(v.x & below);
+    }
+    loc[0] = k;
+#pragma unroll
+    for (int j = 1; j < Q; ++j) {
+        if (bits & (1u << j)) {
+            loc[j] = o.slot[j] + k;
+            continue;
+        }
+        const int dx = cx(j);
+        uint32_t up;
+        if (cy(j) == 0 && cz(j) == 0) {
+            up = dx > 0 ? k - 1u : k + 1u;
+        } else {
+            const int s = row_slot(j);
+            up = dx == 0  ? (uint32_t)rank[s]
+                 : dx > 0 ? (uint32_t)(rank[s] - 1)
+                          : (uint32_t)rank[s] + ((bits >> slot_axis_dir(s)) & 1u ? 0u : 1u);
+        }
+        loc[j] = o.slot[opp(j)] + up;
+    }
+    if (x == 0u || x == o.Lx - 1u) {  // the periodic wrap in x, from the row ends
+#pragma unroll
+        for (int j = 1; j < Q; ++j) {
+            const int dx = cx(j);
+            if (dx == 0 || (bits & (1u << j))) continue;
+            if ((dx > 0 && x != 0u) || (dx < 0 && x != o.Lx - 1u)) continue;
+            const int s = (cy(j) == 0 && cz(j) == 0) ? 8 : row_slot(j);
+            int2 r = make_int2(0, 0);
+            if (!kBoundsCheck ||
+                in_range((uint64_t)((int64_t)p + o.roff[s]), (uint64_t)o.nprows, o.flag))
+                r = __ldg(o.rse[s] + p);
+            // upstream x - 1 of x = 0 is the row's last voxel; x + 1 of
+            // x = Lx - 1 its first
+            loc[j] = o.slot[opp(j)] + (dx > 0 ? (uint32_t)(r.y - 1) : (uint32_t)r.x);
+        }
+    }
+}
+
 // Gathers the 19 populations of one fluid node from `loc`, collides them
 // and stores the post-collision values of the opposite directions back to
 // the same locations (the AA pattern).
