@@ -311,13 +311,14 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- ours
 
-def make_solver(mask, args, layout=None, precision=None, stream=None, max_steps=1_000_000):
+def make_solver(mask, args, layout=None, precision=None, stream=None, max_steps=1_000_000,
+                collision="auto"):
     from paper_1902_11193_gb300 import lbm
 
     return lbm.LBMSolver(mask, "B", 1.0, force=(1e-6, 0.0, 0.0),
                          precision=precision or args.precision, layout=layout or args.layout,
                          check_interval=100, max_steps=max_steps, stream=stream,
-                         block_size=args.block_size)
+                         block_size=args.block_size, collision=collision)
 
 
 def time_production_loop(S, steps, stream):
@@ -334,20 +335,43 @@ def time_production_loop(S, steps, stream):
     return e0.elapsed_time(e1)
 
 
-def time_kernel_launches(S, n, stream):
+def time_kernel_launches(S, n, stream, split=False):
     """Average device time of one plain stream-collide launch (events between
-    consecutive launches on the launching stream)."""
+    consecutive launches on the launching stream).  split=True also returns
+    the mean times of the even-step and odd-step launches (AA patterns: two
+    kernels; AB: the same kernel on both parities)."""
     import torch
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
     torch.cuda.synchronize()
+    p0 = S.steps % 2
     ev[0].record(stream)
     for i in range(n):
         S.step(1)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    d = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
-    return float(np.mean(d)), float(np.min(d))
+    d = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(n)])
+    if not split:
+        return float(np.mean(d)), float(np.min(d))
+    par = (p0 + np.arange(n)) % 2
+    return (float(np.mean(d)), float(np.min(d)), float(np.mean(d[par == 0])),
+            float(np.mean(d[par == 1])))
+
+
+# kernels of each layout's plain stream-collide launches (even step, odd step)
+STEP_KERNELS = {
+    ("sparse", "fp32"): ("k_sparse_even_x2", "k_sparse_odd_l"),
+    ("sparse", "fp16"): ("k_sparse_even_x2", "k_sparse_odd_l"),
+    ("sparse", "fp64"): ("k_sparse", "k_sparse_odd_t"),
+    ("aa", "fp32"): ("k_aa<even>", "k_aa<odd>"), ("aa", "fp16"): ("k_aa<even>", "k_aa<odd>"),
+    ("aa", "fp64"): ("k_aa<even>", "k_aa<odd>"),
+}
+
+
+def collision_form(set_, collision):
+    """The collision the kernels run: the link-basis TRT where the rates have
+    one even and one odd value (Sets B, E, SRT) unless the MRT is forced."""
+    return "trt" if collision == "auto" and set_ in ("B", "E", "SRT") else "mrt"
 
 
 def run_ours(args):
@@ -378,8 +402,9 @@ def run_ours(args):
     k_fp = S.permeability()
     ms = max_over_ranks(dist, ms)
     value = job_throughput(nf, args.steps, ws, ms)
-    # the dominant kernel alone: per-launch event timing on its stream
-    kmean, kmin = time_kernel_launches(S, 50, stream)
+    # the stream-collide launches alone: per-launch event timing on their
+    # stream, even and odd steps apart
+    kmean, kmin, keven, kodd = time_kernel_launches(S, 50, stream, split=True)
     S.close()
     del S
 
@@ -387,6 +412,7 @@ def run_ours(args):
     bpu = BYTES_PER_UPDATE[args.precision]
     achieved = bpu * nf / (kmean * 1e-3) / 1e9
     traffic = measured_traffic(args.layout, args.precision, nf)
+    kern = STEP_KERNELS.get((args.layout, args.precision), ("k_ab", "k_ab"))
 
     out = {
         "metric": "fluid MLUPS", "value": value, "unit": "fluid MLUPS", "n_gpus": ws,
@@ -403,6 +429,17 @@ def run_ours(args):
                      "kernel": f"stream-collide {args.layout} {args.precision}",
                      "algorithmic_bytes_per_launch": bpu * nf,
                      "launch_ms_mean": kmean, "launch_ms_min": kmin,
+                     "launch_ms_even": keven, "launch_ms_odd": kodd,
+                     "frac_even": bpu * nf / (keven * 1e-3) / 1e9 / peak,
+                     "frac_odd": bpu * nf / (kodd * 1e-3) / 1e9 / peak,
+                     "kernel_even": kern[0], "kernel_odd": kern[1],
+                     "dominant": kern[1] if kodd >= keven else kern[0],
+                     "frac_dominant": bpu * nf / (max(kodd, keven) * 1e-3) / 1e9 / peak,
+                     "collision": collision_form("B", "auto"),
+                     "frac_definition": "frac: algorithmic bytes per launch over the mean "
+                                        "launch time of an even and an odd step (one AA "
+                                        "step pair); frac_even, frac_odd, frac_dominant: "
+                                        "per kernel",
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -410,6 +447,17 @@ def run_ours(args):
     }
 
     if rank == 0 and not args.no_extra:
+        # the same workload with the moment-space MRT collision forced
+        S2 = make_solver(mask, args, stream=stream, max_steps=200, collision="mrt")
+        S2.step(warm)
+        m2 = time_production_loop(S2, 200, stream)
+        km, _, ke, ko = time_kernel_launches(S2, 50, stream, split=True)
+        out["mrt"] = {"collision": "mrt", "fluid_MLUPS": nf * 200 / (m2 * 1e-3) / 1e6,
+                      "launch_ms_even": ke, "launch_ms_odd": ko,
+                      "frac": bpu * nf / (km * 1e-3) / 1e9 / peak,
+                      "frac_even": bpu * nf / (ke * 1e-3) / 1e9 / peak,
+                      "frac_odd": bpu * nf / (ko * 1e-3) / 1e9 / peak}
+        S2.close()
         out["layouts"] = {}
         for lay in ("aa", "sparse", "ab"):
             if lay == args.layout:
@@ -567,54 +615,86 @@ def sweep_run(args, stream):
                         "npt2": int(np.sum(npt == 2)), "alone": int(np.sum(npt == 0))}}
 
 
+ADJOINT_SETS = (("B", 3 / 16), ("D", 3 / 16), ("E", 3 / 16), ("E", 3 / 8))
+ADJOINT_TAUS = (0.8, 1.0, 1.3)
+
+
+def adjoint_grads(S, g, set_, lam, tau, F):
+    """Normalised gradients theta (dk/dtheta) / k of one steady adjoint."""
+    k = g["k"]
+    out = {"k": k, "tau_dk_dtau_over_k": g["dtau"] * tau / k,
+           "F_dk_dF_over_k": g["dF"][0] * F / k, "adjoint_iterations": g["iterations"],
+           "adjoint_residual": g["residual"]}
+    if set_ == "D":  # two magic parameters, 3/16 for s_q and 3/8 for s_m at every tau
+        out["Lq_dk_dLq_over_k"] = g["dLambda_q"] * (3 / 16) / k
+        out["Lm_dk_dLm_over_k"] = g["dLambda_m"] * (3 / 8) / k
+    else:  # B (= E(3/16)) and E: one magic parameter for both odd rates
+        out["L_dk_dL_over_k"] = g["dLambda"] * lam / k
+    return out
+
+
 def adjoint_run(args, stream):
     """Steady adjoint on a Boolean medium (r = 6, porosity 0.35, edge
-    --adjoint-size, 128 by default): FP32 forward to the paper's rule, then
-    lbm_adjoint; gradients normalised."""
+    --adjoint-size, 128 by default): for Sets B, D, E(3/16), E(3/8) at
+    tau = 0.8, 1.0, 1.3, the FP32 forward to the two-step-mean rule, then
+    lbm_adjoint; gradients normalised.  Then the transient adjoint of Set D
+    at tau = 1 over the same number of steps."""
     import torch
 
     from paper_1902_11193_gb300 import geometry, lbm
 
     L = args.adjoint_size
+    F = 1e-6
     mask, _ = geometry.boolean(L, 6, 0.35, seed=1902_11193 + 4)
-    res = {"workload": f"boolean-{L}^3 r=6 porosity=0.35, Set D tau=1, F=1e-6, fp32 sparse, "
-                       "two-step-mean stopping rule (tol 1e-8), adjoint tol 1e-6"}
-    S = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision="fp32", layout="sparse",
-                      check_interval=100, stream=stream, stop_rule=1, max_steps=200000)
-    t0 = time.perf_counter()
-    rc, steps = S.run_to_convergence(1e-8, raise_on_failure=False)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    if rc != 0:
-        res.update({"forward_status": rc, "forward_steps": steps})
-        S.close()
-        return res
-    g = S.adjoint(1e-6, max_iter=200000)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    k = g["k"]
     nf = int((mask == 0).sum())
-    res.update({"forward_steps": steps, "forward_s": t1 - t0, "adjoint_iterations": g["iterations"],
-                "adjoint_s": t2 - t1, "adjoint_residual": g["residual"],
-                "adjoint_fluid_MLUPS": nf * g["iterations"] / (t2 - t1) / 1e6,
-                "k": k, "tau_dk_dtau_over_k": g["dtau"] * 1.0 / k,
-                "Lq_dk_dLq_over_k": g["dLambda_q"] * (3 / 16) / k,
-                "Lm_dk_dLm_over_k": g["dLambda_m"] * (3 / 8) / k,
-                "F_dk_dF_over_k": g["dF"][0] * 1e-6 / k})
-    S.close()
+    res = {"workload": f"boolean-{L}^3 r=6 porosity=0.35, F=1e-6 x, fp32 sparse, two-step-mean "
+                       "stopping rule (tol 1e-8), adjoint tol 1e-6; Sets B, D, E(3/16), E(3/8) "
+                       "x tau 0.8, 1.0, 1.3", "grid": []}
+    steps_d1 = None
+    t_fwd = t_adj = 0.0
+    iters = 0
+    for set_, lam in ADJOINT_SETS:
+        for tau in ADJOINT_TAUS:
+            S = lbm.LBMSolver(mask, set_, tau, lam, force=(F, 0, 0), precision="fp32",
+                              layout="sparse", check_interval=100, stream=stream, stop_rule=1,
+                              max_steps=400000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, steps = S.run_to_convergence(1e-8, raise_on_failure=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            row = {"set": set_ if set_ != "E" else f"E({lam:g})", "tau": tau,
+                   "forward_status": rc, "forward_steps": steps}
+            if rc == 0:
+                g = S.adjoint(1e-6, max_iter=400000)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                row.update(adjoint_grads(S, g, set_, lam, tau, F))
+                t_fwd += t1 - t0
+                t_adj += t2 - t1
+                iters += g["iterations"]
+                if set_ == "D" and tau == 1.0:
+                    steps_d1 = steps
+            res["grid"].append(row)
+            S.close()
+    res["forward_s_total"] = t_fwd
+    res["adjoint_s_total"] = t_adj
+    res["adjoint_fluid_MLUPS"] = nf * iters / t_adj / 1e6 if t_adj > 0 else None
+    if steps_d1 is None:
+        return res
     # transient adjoint: the gradient of k after the same number of steps
     # from rest, by a checkpointed reverse sweep
-    T = lbm.LBMSolver(mask, "D", 1.0, force=(1e-6, 0, 0), precision="fp32", layout="sparse",
+    T = lbm.LBMSolver(mask, "D", 1.0, force=(F, 0, 0), precision="fp32", layout="sparse",
                       stream=stream)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
-    gt = T.adjoint_transient(steps)
+    gt = T.adjoint_transient(steps_d1)
     torch.cuda.synchronize()
     t4 = time.perf_counter()
     res["transient"] = {
-        "steps": steps, "wall_s": t4 - t3,
+        "set": "D", "tau": 1.0, "steps": steps_d1, "wall_s": t4 - t3,
         # forward sweep, recomputation of every segment, adjoint step: three passes
-        "fluid_MLUPS_per_pass": 3 * nf * steps / (t4 - t3) / 1e6,
+        "fluid_MLUPS_per_pass": 3 * nf * steps_d1 / (t4 - t3) / 1e6,
         "k": gt["k"], "tau_dk_dtau_over_k": gt["dtau"] * 1.0 / gt["k"],
         "Lq_dk_dLq_over_k": gt["dLambda_q"] * (3 / 16) / gt["k"],
         "Lm_dk_dLm_over_k": gt["dLambda_m"] * (3 / 8) / gt["k"]}
@@ -731,6 +811,42 @@ def large_run(args, stream):
         S.close()
         torch.cuda.synchronize()
     res["fp16_vs_fp32_mean_velocity_rel_diff_after_50_steps"] = abs(U["fp16"] - U["fp32"]) / abs(U["fp32"])
+    res["k_error"] = reduced_precision_k_errors(stream)
+    return res
+
+
+def reduced_precision_k_errors(stream, L=256):
+    """Permeability of a converged sample with the 1024^3 workload's recipe
+    (Boolean medium, r = 8, porosity 0.20, Set D, tau = 1, F = 1e-6, sparse),
+    at edge L: FP64 to the two-step-mean rule (tol 1e-8, K = 100), then FP32
+    and FP16 storage for the same number of steps; each k (the two-step mean
+    of the last chunk) against the FP64 one."""
+    import torch
+
+    from paper_1902_11193_gb300 import geometry, lbm
+
+    mask, _ = geometry.boolean(L, 8, 0.20, seed=1902_11193 + 5)
+    kw = dict(force=(1e-6, 0, 0), layout="sparse", check_interval=100, stream=stream,
+              stop_rule=1)
+    t0 = time.perf_counter()
+    S = lbm.LBMSolver(mask, "D", 1.0, precision="fp64", max_steps=400000, **kw)
+    rc, steps = S.run_to_convergence(1e-8, raise_on_failure=False)
+    k64 = S.converged_permeability()[0]
+    S.close()
+    res = {"workload": f"boolean-{L}^3 r=8 porosity=0.20 seed={1902_11193 + 5}, Set D tau=1, "
+                       "F=1e-6, sparse; FP64 to tol 1e-8 (two-step mean, K=100), FP32 and "
+                       "FP16 storage for the same steps",
+           "fluid_nodes": int((mask == 0).sum()), "fp64_status": rc, "steps": steps,
+           "k_fp64": k64}
+    for prec in ("fp32", "fp16"):
+        S = lbm.LBMSolver(mask, "D", 1.0, precision=prec, max_steps=steps, **kw)
+        S.run_to_convergence(0.0, raise_on_failure=False)
+        k = S.converged_permeability()[0]
+        res[f"k_{prec}"] = k
+        res[f"{prec}_rel_err"] = abs(k - k64) / abs(k64)
+        S.close()
+    torch.cuda.synchronize()
+    res["wall_s"] = time.perf_counter() - t0
     return res
 
 

@@ -49,13 +49,17 @@ def build_geometry(force: bool = False) -> str:
     return GEOM_SO
 
 
-def build_lbm(force: bool = False, extra_flags: list[str] | None = None) -> str:
+def build_lbm(force: bool = False, extra_flags: list[str] | None = None,
+              out: str | None = None) -> str:
+    """Builds liblbm_gb300.so (or, with `out`, a variant such as the
+    bounds-check build, -DLBM_BOUNDS_CHECK, at that path, objects beside it)."""
+    so = out or LBM_SO
     srcs = [os.path.join(CSRC, s) for s in CUDA_SOURCES]
     deps = srcs + [os.path.join(CSRC, h) for h in CUDA_HEADERS] + [os.path.join(INCLUDE, "lbm.h")]
-    if not (force or _stale(LBM_SO, deps)):
-        return LBM_SO
-    os.makedirs(LIBDIR, exist_ok=True)
-    objdir = os.path.join(LIBDIR, "obj")
+    if not (force or _stale(so, deps)):
+        return so
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    objdir = os.path.join(os.path.dirname(so), "obj")
     os.makedirs(objdir, exist_ok=True)
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *NVCC_ARCH,
              "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr", *(extra_flags or [])]
@@ -67,10 +71,21 @@ def build_lbm(force: bool = False, extra_flags: list[str] | None = None) -> str:
 
     with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LBM_SO + f".tmp{os.getpid()}"
+    tmp = so + f".tmp{os.getpid()}"
     subprocess.run([_nvcc(), "-shared", *NVCC_ARCH, "-o", tmp, *objs, "-lcudart"], check=True)
-    os.replace(tmp, LBM_SO)
-    return LBM_SO
+    os.replace(tmp, so)
+    return so
+
+
+BOUNDS_SO = os.path.join(LIBDIR, "bounds", "liblbm_gb300.so")
+
+
+def build_bounds_check(force: bool = False) -> str:
+    """The bounds-check build: every computed population, index-record,
+    row-word and row-start offset range-checked before the access (the
+    device flag's bit 1 on a miss, lbm_device_flags).  A debugging aid, not
+    loaded by the package."""
+    return build_lbm(force, ["-DLBM_BOUNDS_CHECK"], out=BOUNDS_SO)
 
 
 def build_all(force: bool = False) -> None:

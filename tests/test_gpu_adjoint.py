@@ -101,43 +101,76 @@ def boolean48(geom):
     return geom.boolean(48, 6, 0.35, seed=1902_11193 + 4)[0]
 
 
+def _magic_rates(L, st, tau, lam, Lq=None, Lm=None):
+    """Table 2 rates of the set, with the odd rates s_q and s_m set through
+    their own magic parameters where given (Set E's formula, Sec. 2.3)."""
+    s = L.rates(st, tau, lam)
+    if Lq is not None:
+        s[[4, 6, 8]] = L.rates("E", tau, Lq)[4]
+    if Lm is not None:
+        s[[16, 17, 18]] = L.rates("E", tau, Lm)[16]
+    return s
+
+
 def _fd(L, mask, st, tau, lam, F, which, h=1e-4):
     """Central difference of the FP64 permeability at the fixed point (the
-    two-step mean the stopping rule converged on, to 1e-12)."""
-    def k_at(t, l, Fv):
-        S = L.LBMSolver(mask, st, t, l, Fv, precision="fp64", layout="sparse", check_interval=20,
-                        max_steps=100000, stop_rule=1)
+    two-step mean the stopping rule converged on, to 1e-12).  h is an
+    absolute step in tau and the magic parameters, a relative one in F."""
+    def k_at(t=tau, Fv=F, Lq=None, Lm=None):
+        kw = dict(precision="fp64", layout="sparse", check_interval=20, max_steps=100000,
+                  stop_rule=1)
+        if Lq is None and Lm is None:
+            S = L.LBMSolver(mask, st, t, lam, Fv, **kw)
+        else:
+            S = L.LBMSolver(mask, force=Fv, rates_=_magic_rates(L, st, t, lam, Lq, Lm), **kw)
         rc, _ = S.run_to_convergence(1e-12)
         assert rc == 0
-        return S.converged_permeability()[0]
+        k = S.converged_permeability()[0]
+        S.close()
+        return k
     if which == "dtau":
-        return (k_at(tau + h, lam, F) - k_at(tau - h, lam, F)) / (2 * h)
-    if which == "dLambda":
-        return (k_at(tau, lam + h, F) - k_at(tau, lam - h, F)) / (2 * h)
+        return (k_at(t=tau + h) - k_at(t=tau - h)) / (2 * h)
+    if which == "dLambda":  # Sets B, E: both odd rates through one parameter
+        return (k_at(Lq=lam + h, Lm=lam + h) - k_at(Lq=lam - h, Lm=lam - h)) / (2 * h)
+    if which == "dLambda_q":  # Set D: Lambda_q = 3/16
+        return (k_at(Lq=3 / 16 + h) - k_at(Lq=3 / 16 - h)) / (2 * h)
+    if which == "dLambda_m":  # Set D: Lambda_m = 3/8
+        return (k_at(Lm=3 / 8 + h) - k_at(Lm=3 / 8 - h)) / (2 * h)
     Fp, Fm = (F[0] * (1 + h), 0, 0), (F[0] * (1 - h), 0, 0)
-    return (k_at(tau, lam, Fp) - k_at(tau, lam, Fm)) / (2 * h * F[0])
+    return (k_at(Fv=Fp) - k_at(Fv=Fm)) / (2 * h * F[0])
 
 
-@pytest.mark.parametrize("st,lam,tau", [("B", 3 / 16, 0.8), ("D", 3 / 16, 1.3), ("E", 3 / 8, 1.0)])
+# the adjoint study's grid: Sets B, D, E(3/8) at tau = 0.8, 1.0, 1.3
+FD_GRID = [(st, lam, tau) for st, lam in (("B", 3 / 16), ("D", 3 / 16), ("E", 3 / 8))
+           for tau in (0.8, 1.0, 1.3)]
+
+
+@pytest.mark.parametrize("st,lam,tau", FD_GRID)
 def test_fp32_adjoint_vs_finite_differences_48(L, boolean48, st, lam, tau):
+    """FP32 forward and adjoint against FP64 central differences (h = 1e-4)
+    of the converged permeability, every gradient component, normalised
+    (theta dk/dtheta / k) within 1e-4."""
     F = (1e-6, 0.0, 0.0)
     k, g, S = _gpu_grad(L, boolean48, st, tau, lam, F, precision="fp32", layout="sparse", tol=1e-8,
                         atol=1e-6, rule=1)
-    checks = ["dtau", "dF"] + (["dLambda"] if st == "E" else [])
+    checks = ["dtau", "dF"] + (["dLambda_q", "dLambda_m"] if st == "D" else ["dLambda"])
     for key in checks:
         fd = _fd(L, boolean48, st, tau, lam, F, key)
-        scale = {"dtau": tau, "dLambda": lam, "dF": F[0]}[key]
+        scale = {"dtau": tau, "dLambda": lam, "dLambda_q": 3 / 16, "dLambda_m": 3 / 8,
+                 "dF": F[0]}[key]
         adj = g["dF"][0] if key == "dF" else g[key]
         err = abs(adj * scale / k - fd * scale / k)
         print(f"{st} tau={tau} {key}: adjoint {adj * scale / k:+.6e} fd {fd * scale / k:+.6e}"
               f" err {err:.2e}")
         assert err < 1e-4
+    S.close()
 
 
-def test_adjoint_boolean_vs_oracle(L, ora, geom):
-    """32^3 Boolean medium (r = 4, porosity 0.35): the CPU adjoint stays within
-    a minute; FP64 and FP32 GPU adjoints against it."""
-    mask = geom.boolean(32, 4, 0.35, seed=1902_11193 + 4)[0]
+def test_adjoint_boolean_vs_oracle(L, ora, boolean48):
+    """The 48^3 Boolean medium of the adjoint study (r = 6, porosity 0.35),
+    Set D at tau = 1: FP64 and FP32 GPU adjoints against the oracle's
+    adjoint (about a minute of host time)."""
+    mask = boolean48
     st, tau, lam = "D", 1.0, 3 / 16
     F = (1e-6, 0.0, 0.0)
     O = ora.Solver(mask, ora.rates(st, tau, lam), F)
