@@ -340,7 +340,17 @@ typedef struct {
                                    the autotuner times that faster than the batched
                                    kernel: 1 (default) let it choose, 0 never, 2 always
                                    (every autotuned lattice runs alone, whatever its
-                                   size) */
+                                   size).  The stepwise schedule needs no lone runs, so
+                                   with it the default offers none. */
+    int32_t schedule;           /* 0 (default): per chunk, the stepwise schedule while
+                                   the active lattices hold at least four waves of the
+                                   persistent kernel's threads (FP32), the persistent
+                                   kernel below that; 1: always the persistent kernel;
+                                   2: always stepwise (FP32 only).  Stepwise: per step,
+                                   one launch per class of lattices (layout x collision
+                                   form x parity) of the multi-lattice twins of the
+                                   single-lattice kernels; no grid barrier.  Results are
+                                   bitwise the same under either schedule. */
 } lbm_batch_options;
 
 typedef struct lbm_batch lbm_batch;
@@ -366,8 +376,10 @@ int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *nodes_per_thread);
 /* The context of lattice i (owned by the batch; valid until lbm_batch_destroy),
  * for the single-lattice readers (populations, velocity, checkpoint). */
 lbm_ctx *lbm_batch_lattice(lbm_batch *b, int32_t i);
-/* Persistent-kernel launches and graph replays so far (launch accounting). */
+/* Kernel launches and graph replays so far (launch accounting). */
 int64_t lbm_batch_kernel_launches(const lbm_batch *b);
+/* Chunks run under each schedule so far (nullable outputs). */
+int lbm_batch_schedule_counts(const lbm_batch *b, int64_t *stepwise, int64_t *persistent);
 void lbm_batch_destroy(lbm_batch *b);
 
 /* Number of CUDA kernels this context has launched (for launch accounting). */

@@ -926,3 +926,14 @@ const char *lbm_strerror(int code) {
 const char *lbm_last_cuda_error(void) { return g_cuda_err; }
 
 }  // extern "C"
+
+namespace lbm {
+// One chunk of the convergence loop for a batch member that runs with the
+// single-lattice kernels: `plain` plain steps, then `nmeas` measuring steps
+// into slots 0 .. nmeas - 1 of c->d_U, replayed from the context's chunk
+// graphs like lbm_run_to_convergence's chunks.  Advances c->steps.
+int enqueue_measured_chunk(lbm_ctx *c, int64_t plain, int nmeas) {
+    c->converged = c->has_conv = false;
+    return enqueue_chunk(c, plain, 0, nmeas);
+}
+}  // namespace lbm

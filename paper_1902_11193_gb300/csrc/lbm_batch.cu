@@ -39,11 +39,13 @@ namespace lbm {
 
 SparseMap sparse_map(const lbm_ctx *c);
 int launch_step(lbm_ctx *c, bool reduce);
+int enqueue_measured_chunk(lbm_ctx *c, int64_t plain, int nmeas);
 
 struct BatchLat {
     int layout;  // LBM_LAYOUT_AA or LBM_LAYOUT_SPARSE
-    int npt;     // units per thread per tile
+    int npt;     // units per thread per tile (persistent kernel)
     uint32_t units;
+    uint32_t goff;  // first of the lattice's 256-unit groups in the stepwise partials
     void *pop;
     const uint32_t *lw;
     SparseMap sm;
@@ -213,9 +215,188 @@ __global__ void __launch_bounds__(1024) k_batch_finalize(const BatchLat *__restr
     }
 }
 
+// ------------------------------------------------------ stepwise schedule
+//
+// Where the active lattices hold enough units to fill the GPU many times
+// over, a grid barrier per step buys nothing over a kernel boundary, while
+// the persistent kernel pays for its generality: populations through L2
+// only, one unit per thread, both collision forms in one kernel and its
+// register cap.  The stepwise schedule instead launches, per step, one
+// kernel per class of lattices (layout x collision form x parity), each the
+// multi-lattice twin of a single-lattice kernel: the two-node even step and
+// the tiled odd step of the sparse layout, the dense AA step.  A block takes
+// one tile of one lattice.  Per-node arithmetic and the per-256-unit group
+// sums are those of the single-lattice kernels, and the partials of lattice i
+// sit at part[slot][goff_i + group], summed in the single-lattice finalize's
+// order, so members stay bitwise equal to lone runs.
+
+#ifndef LBM_STEP_EVEN_NPT
+#define LBM_STEP_EVEN_NPT 2
+#endif
+#ifndef LBM_STEP_ODD_MIN_BLOCKS
+#define LBM_STEP_ODD_MIN_BLOCKS 3
+#endif
+constexpr uint32_t kEvenTile = 256 * LBM_STEP_EVEN_NPT;  // sparse even steps
+constexpr uint32_t kOddTile = 1024;   // sparse odd steps: four units per thread
+constexpr uint32_t kDenseTile = 256;  // dense AA steps: one unit per thread
+
+struct StepRed {
+    double *part;   // [nmeas][total groups][3], or nullptr on plain steps
+    int slot;
+    uint32_t ngroups;  // total groups (the slot stride)
+};
+
+__device__ __forceinline__ double *group_partial(const StepRed &r, const BatchLat &L, uint32_t g) {
+    return r.part + 3 * ((size_t)r.slot * r.ngroups + L.goff + g);
+}
+
+template <typename S, int K, bool RED>
+__global__ void __launch_bounds__(256, LBM_STEP_EVEN_NPT == 2 ? 2 : 3)
+    k_step_sparse_even(const BatchLat *__restrict__ lats, const Tile *__restrict__ tiles, StepRed red) {
+    using C = typename Store<S>::C;
+    const Tile tl = tiles[blockIdx.x];
+    const BatchLat &L = lats[tl.lat];
+    // the lattice's collision parameters in shared memory: read where used,
+    // instead of held in registers for the whole kernel
+    __shared__ Collide<C> p;
+    if (threadIdx.x == 0) p = lat_params<C>(L);
+    __syncthreads();
+    S *A = (S *)L.pop;
+    const uint32_t Nf = L.units;
+    const uint32_t k0 = tl.first + threadIdx.x, k1 = k0 + 256u;
+    const bool v0 = k0 < Nf, v1 = LBM_STEP_EVEN_NPT == 2 && k1 < Nf;
+    C g0[Q], g1[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) g0[j] = v0 ? Store<S>::ld(A + (uint32_t)j * Nf + k0, 1.f) : C(0);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) g1[j] = v1 ? Store<S>::ld(A + (uint32_t)j * Nf + k1, 1.f) : C(0);
+    C jx0 = C(0), jy0 = C(0), jz0 = C(0), jx1 = C(0), jy1 = C(0), jz1 = C(0);
+    if (v0) {
+        collide_as<K, C>(g0, p, jx0, jy0, jz0);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) Store<S>::st(A + (uint32_t)j * Nf + k0, g0[opp(j)], 1.f);
+    }
+    if (v1) {
+        collide_as<K, C>(g1, p, jx1, jy1, jz1);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) Store<S>::st(A + (uint32_t)j * Nf + k1, g1[opp(j)], 1.f);
+    }
+    if (RED) {
+        __shared__ double wsum[2][8][3];
+        warp_momentum_store<C>(jx0, jy0, jz0, v0, wsum[0], L.sm.flag);
+        warp_momentum_store<C>(jx1, jy1, jz1, v1, wsum[1], L.sm.flag);
+        __syncthreads();
+        const uint32_t g = tl.first / 256u;
+        const int ng = LBM_STEP_EVEN_NPT == 2 && (g + 1u) * 256u < Nf ? 2 : 1;
+        if ((int)threadIdx.x < 3 * ng) {
+            const int r = threadIdx.x / 3, a = threadIdx.x % 3;
+            group_partial(red, L, g + (uint32_t)r)[a] = group_momentum_total(wsum[r], a);
+        }
+    }
+}
+
+template <typename S, int K, bool RED>
+__global__ void __launch_bounds__(256, LBM_STEP_ODD_MIN_BLOCKS)
+    k_step_sparse_odd(const BatchLat *__restrict__ lats, const Tile *__restrict__ tiles, StepRed red) {
+    using C = typename Store<S>::C;
+    constexpr int NPT = (int)(kOddTile / 256);
+    __shared__ double wsum[RED ? NPT : 1][8][3];
+    const Tile tl = tiles[blockIdx.x];
+    const BatchLat &L = lats[tl.lat];
+    __shared__ Collide<C> p;
+    if (threadIdx.x == 0) p = lat_params<C>(L);
+    __syncthreads();
+    S *A = (S *)L.pop;
+    const SparseMap &m = L.sm;
+    const uint32_t Nf = L.units;
+    uint32_t k = tl.first + threadIdx.x;
+    uint2 nxt = k < Nf ? __ldg(m.nb + k) : make_uint2(0u, 0u);
+    const uint32_t g0 = tl.first / 256u;
+    int groups = 0;
+#pragma unroll 1
+    for (int r = 0; r < NPT; ++r, k += 256u) {
+        if ((g0 + (uint32_t)r) * 256u >= Nf) break;  // block-uniform
+        const bool valid = k < Nf;
+        const uint2 cur = nxt;
+        if (r + 1 < NPT && k + 256u < Nf) nxt = __ldg(m.nb + k + 256u);
+        C jx = C(0), jy = C(0), jz = C(0);
+        if (valid)
+            aa_sparse_update<S, true, uint32_t, Store<S>, K>(A, m, Nf, k, cur, p, 1.f, 1.f, jx, jy, jz);
+        if (RED) warp_momentum_store<C>(jx, jy, jz, valid, wsum[RED ? r : 0], L.sm.flag);
+        ++groups;
+    }
+    if (RED) {
+        __syncthreads();
+        if ((int)threadIdx.x < 3 * groups) {
+            const int r = threadIdx.x / 3, a = threadIdx.x % 3;
+            group_partial(red, L, g0 + (uint32_t)r)[a] = group_momentum_total(wsum[r], a);
+        }
+    }
+}
+
+template <typename S, bool ODD, int K, bool RED>
+__global__ void __launch_bounds__(256)
+    k_step_dense(const BatchLat *__restrict__ lats, const Tile *__restrict__ tiles, StepRed red) {
+    using C = typename Store<S>::C;
+    const Tile tl = tiles[blockIdx.x];
+    const BatchLat &L = lats[tl.lat];
+    __shared__ Collide<C> p;
+    if (threadIdx.x == 0) p = lat_params<C>(L);
+    __syncthreads();
+    const uint32_t n = tl.first + threadIdx.x;
+    const uint32_t w = n < L.units ? L.lw[n] : SOLID_BIT;
+    C jx = C(0), jy = C(0), jz = C(0);
+    const bool fluid = aa_dense_update<S, ODD, Store<S>, K>((S *)L.pop, n, w, L.d, p, 1.f, 1.f, jx,
+                                                            jy, jz, L.sm.flag);
+    if (RED) block_momentum_sum<C>(jx, jy, jz, fluid, group_partial(red, L, tl.first / 256u),
+                                   L.sm.flag);
+}
+
+// U[i][slot][a] for the lattices flagged in `want`: the sum of lattice i's
+// group partials of each measured slot over N_i, in the single-lattice
+// finalize's order (thread t adds groups t, t + 1024, ..., then a fixed
+// shared-memory tree).
+__global__ void __launch_bounds__(1024) k_step_finalize(const BatchLat *__restrict__ lats,
+                                                        const char *__restrict__ want,
+                                                        const double *__restrict__ part,
+                                                        uint32_t ngroups, int nmeas, double *U) {
+    const int i = blockIdx.x;
+    if (!want[i]) return;
+    const uint32_t ng = (lats[i].units + 255u) / 256u;
+    __shared__ double sm[3][1024];
+    for (int slot = 0; slot < nmeas; ++slot) {
+        const double *pp = part + 3 * ((size_t)slot * ngroups + lats[i].goff);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (uint32_t b = threadIdx.x; b < ng; b += blockDim.x)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a] += pp[3 * (size_t)b + a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] = acc[a];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] += sm[a][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x < 3) U[(size_t)9 * i + 3 * slot + threadIdx.x] = sm[threadIdx.x][0] * lats[i].inv_N;
+        __syncthreads();
+    }
+}
+
 }  // namespace lbm
 
 using namespace lbm;
+
+// One class of the stepwise schedule: lattices of one layout and collision
+// form whose step count had parity `parity` at the chunk's start.  Sparse
+// classes keep an even-step and an odd-step tile list, dense classes one.
+struct StepClass {
+    int layout, trt;
+    int rep;               // a member lattice: its step count gives the class's parity
+    int even_off, even_n;  // tiles in d_step_tiles
+    int odd_off, odd_n;
+};
 
 struct lbm_batch {
     int n;
@@ -245,6 +426,17 @@ struct lbm_batch {
     bool failed;
     int64_t launches;
     uint64_t timeout_ns;
+    // stepwise schedule
+    std::vector<StepClass> classes;
+    std::vector<int> group_end;  // classes of group g: [group_end[g-1], group_end[g])
+    std::vector<int> direct;     // active lattices stepped with their own kernels
+    Tile *d_step_tiles;
+    int max_step_tiles;
+    double *d_step_part;
+    uint32_t ngroups;
+    char *d_want;
+    int64_t stepwise_chunks, persistent_chunks;
+    std::vector<uint32_t> goff;
 };
 
 extern "C" {
@@ -262,6 +454,7 @@ void lbm_batch_default_options(lbm_batch_options *o) {
     o->test_skip_block = -1;
     o->stop_rule = 0;
     o->solo = 1;
+    o->schedule = 0;
 }
 
 void lbm_batch_destroy(lbm_batch *b) {
@@ -277,6 +470,9 @@ void lbm_batch_destroy(lbm_batch *b) {
     cudaFree(b->d_tile_part);
     cudaFree(b->d_bar);
     cudaFree(b->d_U);
+    cudaFree(b->d_step_tiles);
+    cudaFree(b->d_step_part);
+    cudaFree(b->d_want);
     cudaFreeHost(b->h_steps);
     cudaFreeHost(b->h_U);
     cudaFreeHost(b->h_err);
@@ -316,6 +512,245 @@ int coop_grid(int precision) {
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 256, 0);
     return sms * (per > 0 ? per : 1);
+}
+
+// ---- stepwise schedule (host side)
+
+uint32_t groups_of(const BatchLat &L) { return (L.units + 255u) / 256u; }
+bool lat_trt(const lbm_batch *b, const BatchLat &L) {
+    return b->opt.precision == LBM_FP64 ? L.pd.trt != 0 : L.pf.trt != 0;
+}
+
+// Tiles of lattice i for the stepwise kernels: sparse lattices an even-step
+// list (kEvenTile units per tile) and an odd-step list (kOddTile), dense
+// lattices one list (kDenseTile).
+void step_tiles_of(const BatchLat &L, int i, std::vector<Tile> &even, std::vector<Tile> &odd) {
+    if (L.layout == LBM_LAYOUT_SPARSE) {
+        for (uint32_t u = 0; u < L.units; u += kEvenTile) even.push_back(Tile{i, u});
+        for (uint32_t u = 0; u < L.units; u += kOddTile) odd.push_back(Tile{i, u});
+    } else {
+        for (uint32_t u = 0; u < L.units; u += kDenseTile) even.push_back(Tile{i, u});
+    }
+}
+
+// Launches one stepwise kernel over `n` tiles of one class at parity par.
+cudaError_t launch_step_kernel(cudaStream_t st, const BatchLat *d_lats, const Tile *tiles, int n,
+                               int layout, bool trt, int par, const StepRed &red) {
+    if (n <= 0) return cudaSuccess;
+    const bool R = red.part != nullptr;
+#define LBM_STEP_LAUNCH(KERNEL, ...)                                                             \
+    do {                                                                                         \
+        if (trt) {                                                                               \
+            if (R) KERNEL<__VA_ARGS__, kCollideTrt, true><<<n, 256, 0, st>>>(d_lats, tiles, red); \
+            else KERNEL<__VA_ARGS__, kCollideTrt, false><<<n, 256, 0, st>>>(d_lats, tiles, red);  \
+        } else {                                                                                 \
+            if (R) KERNEL<__VA_ARGS__, kCollideMrt, true><<<n, 256, 0, st>>>(d_lats, tiles, red); \
+            else KERNEL<__VA_ARGS__, kCollideMrt, false><<<n, 256, 0, st>>>(d_lats, tiles, red);  \
+        }                                                                                        \
+    } while (0)
+    if (layout == LBM_LAYOUT_SPARSE) {
+        if (par == 0) LBM_STEP_LAUNCH(k_step_sparse_even, float);
+        else LBM_STEP_LAUNCH(k_step_sparse_odd, float);
+    } else {
+        if (par == 0) LBM_STEP_LAUNCH(k_step_dense, float, false);
+        else LBM_STEP_LAUNCH(k_step_dense, float, true);
+    }
+#undef LBM_STEP_LAUNCH
+    return cudaGetLastError();
+}
+
+// Bytes a lattice's steps touch: its populations and, per unit, the index
+// record or link word.
+size_t lat_bytes(const lbm_batch *b, const BatchLat &L) {
+    const size_t elem = b->opt.precision == LBM_FP64 ? 8 : 4;
+    return (size_t)L.units * (Q * elem + (L.layout == LBM_LAYOUT_SPARSE ? 8 : 4));
+}
+
+// A lattice with at least this many units fills the GPU by itself: under the
+// stepwise schedule it runs each chunk with its own single-lattice kernels
+// (whose parameters sit in the constant bank; at 96^3 they stepped 40%
+// faster than the multi-lattice kernels with one lattice per launch), on
+// the batch's stream, its chunk replayed from its own CUDA graph.
+#ifndef LBM_STEP_DIRECT_UNITS
+#define LBM_STEP_DIRECT_UNITS 300000
+#endif
+constexpr int64_t kDirectUnits = LBM_STEP_DIRECT_UNITS;
+
+// Share of the L2 cache a group of lattices may fill (percent).
+#ifndef LBM_STEP_L2_PERCENT
+#define LBM_STEP_L2_PERCENT 60
+#endif
+
+// Rebuilds the groups, classes and tile lists of the active lattices.  The
+// active lattices are packed, in order, into groups whose states together
+// fit LBM_STEP_L2_PERCENT of the L2 cache (a larger lattice is a group of
+// its own); a chunk runs each group through all its steps before the next,
+// so a group's populations stay in L2 from one step to the next.
+cudaError_t upload_step_tiles(lbm_batch *b, const std::vector<BatchLat> &lats) {
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t budget = (size_t)(l2 > 0 ? l2 : (64 << 20)) * LBM_STEP_L2_PERCENT / 100;
+    std::vector<char> want(b->n, 0);
+    std::vector<Tile> all;
+    b->classes.clear();
+    b->group_end.clear();
+    size_t used = 0;
+    std::map<int, std::pair<std::vector<Tile>, std::vector<Tile>>> lists;
+    std::map<int, int> rep;
+    auto flush = [&]() {
+        for (auto &kv : lists) {
+            StepClass c;
+            c.layout = kv.first / 4;
+            c.trt = (kv.first >> 1) & 1;
+            c.rep = rep[kv.first];
+            c.even_off = (int)all.size();
+            c.even_n = (int)kv.second.first.size();
+            all.insert(all.end(), kv.second.first.begin(), kv.second.first.end());
+            c.odd_off = (int)all.size();
+            c.odd_n = (int)kv.second.second.size();
+            all.insert(all.end(), kv.second.second.begin(), kv.second.second.end());
+            b->classes.push_back(c);
+        }
+        if (!lists.empty()) b->group_end.push_back((int)b->classes.size());
+        lists.clear();
+        rep.clear();
+        used = 0;
+    };
+    b->direct.clear();
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->active[i]) continue;
+        if ((int64_t)lats[i].units >= kDirectUnits) {  // fills the GPU by itself
+            b->direct.push_back(i);
+            continue;
+        }
+        want[i] = 1;
+        const size_t bytes = lat_bytes(b, lats[i]);
+        if (used > 0 && used + bytes > budget) flush();
+        used += bytes;
+        const int key = lats[i].layout * 4 + (lat_trt(b, lats[i]) ? 2 : 0) + (int)(b->ctx[i]->steps & 1);
+        auto &l = lists[key];
+        step_tiles_of(lats[i], i, l.first, l.second);
+        rep.emplace(key, i);
+    }
+    flush();
+    cudaError_t e = cudaSuccess;
+    if (!all.empty())
+        e = cudaMemcpyAsync(b->d_step_tiles, all.data(), sizeof(Tile) * all.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_want, want.data(), (size_t)b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors go out of scope
+    return e;
+}
+
+// One chunk of K steps under the stepwise schedule: per step one launch per
+// class, the last nmeas steps measuring; then the per-lattice sums and the
+// copy of the results.
+cudaError_t enqueue_step_chunk(lbm_batch *b) {
+    const int K = b->opt.check_interval;
+    const int nmeas = b->opt.stop_rule == 1 ? 3 : 2;
+    for (const int i : b->direct) {  // lattices that fill the GPU alone
+        lbm_ctx *c = b->ctx[i];
+        const int64_t l0 = c->launches;
+        const int rc = enqueue_measured_chunk(c, K - nmeas, nmeas);
+        if (rc != LBM_OK) return cudaErrorUnknown;
+        b->launches += c->launches - l0;
+    }
+    int c0 = 0;
+    for (const int c1 : b->group_end) {  // the groups one after another
+        for (int s = 0; s < K; ++s) {
+            const int slot = s - (K - nmeas);
+            StepRed red{slot >= 0 ? b->d_step_part : nullptr, slot, b->ngroups};
+            for (int ci = c0; ci < c1; ++ci) {
+                const StepClass &c = b->classes[ci];
+                const int par = (int)((b->ctx[c.rep]->steps + s) & 1);
+                const bool odd_list = c.layout == LBM_LAYOUT_SPARSE && par == 1;
+                cudaError_t e = launch_step_kernel(
+                    b->stream, b->d_lats, b->d_step_tiles + (odd_list ? c.odd_off : c.even_off),
+                    odd_list ? c.odd_n : c.even_n, c.layout, c.trt != 0, par, red);
+                if (e != cudaSuccess) return e;
+                b->launches++;
+            }
+        }
+        c0 = c1;
+    }
+    k_step_finalize<<<b->n, 1024, 0, b->stream>>>(b->d_lats, b->d_want, b->d_step_part, b->ngroups,
+                                                  nmeas, b->d_U);
+    b->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *b->h_err = 0;
+    e = cudaMemcpyAsync(b->h_U, b->d_U, sizeof(double) * 9 * b->n, cudaMemcpyDeviceToHost,
+                        b->stream);
+    for (const int i : b->direct)  // their measured slots, after the bulk copy
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_U + 9 * (size_t)i, b->ctx[i]->d_U, sizeof(double) * 3 * nmeas,
+                                cudaMemcpyDeviceToHost, b->stream);
+    return e;
+}
+
+// Active lattices hold at least this many units: run the chunk stepwise
+// (four waves of the persistent kernel's resident threads).
+int64_t stepwise_min_units(const lbm_batch *b) { return 4 * (int64_t)b->grid * kTileThreads; }
+
+// Autotuner for the stepwise schedule: device time of `steps` steps of the
+// stepwise kernels over enough copies of lattice c's tiles to fill the GPU
+// (about four waves), per copy.  The copies update the same populations, so
+// the scratch context's values are meaningless afterwards; only the time
+// is used.
+float time_candidate_step(lbm_batch *b, lbm_ctx *c, int steps) {
+    BatchLat L = make_lat(c, 1);
+    L.goff = 0;
+    // copies up to four waves of threads, within one group's share of L2
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const int64_t budget = (int64_t)(l2 > 0 ? l2 : (64 << 20)) * LBM_STEP_L2_PERCENT / 100;
+    const int64_t target = stepwise_min_units(b);
+    const int64_t units = L.units ? L.units : 1;
+    int64_t R = (target + units - 1) / units;
+    const int64_t fit = budget / (int64_t)(lat_bytes(b, L) ? lat_bytes(b, L) : 1);
+    if (R > fit) R = fit;
+    if (R < 1) R = 1;
+    std::vector<Tile> even, odd;
+    for (int r = 0; r < R; ++r) step_tiles_of(L, 0, even, odd);
+    BatchLat *d_l = nullptr;
+    Tile *d_t = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = INFINITY;
+    const size_t nt = even.size() + odd.size();
+    if (cudaMalloc(&d_l, sizeof L) == cudaSuccess && cudaMalloc(&d_t, sizeof(Tile) * nt) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        cudaMemcpyAsync(d_l, &L, sizeof L, cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(d_t, even.data(), sizeof(Tile) * even.size(), cudaMemcpyHostToDevice, b->stream);
+        if (!odd.empty())
+            cudaMemcpyAsync(d_t + even.size(), odd.data(), sizeof(Tile) * odd.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+        const StepRed none{nullptr, 0, 0};
+        const bool trt = lat_trt(b, L);
+        cudaError_t e = cudaSuccess;
+        cudaEventRecord(e0, b->stream);
+        for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+            const int par = s & 1;
+            const bool ol = L.layout == LBM_LAYOUT_SPARSE && par == 1;
+            e = launch_step_kernel(b->stream, d_l, ol ? d_t + even.size() : d_t,
+                                   (int)(ol ? odd.size() : even.size()), L.layout, trt, par, none);
+            b->launches++;
+        }
+        cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess) {
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)R;  // per copy
+        }
+        cudaGetLastError();
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_l);
+    cudaFree(d_t);
+    return ms;
 }
 
 // Uploads the tile table of the active lattices.
@@ -469,6 +904,8 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     if (o.stop_rule != 0 && o.stop_rule != 1) return LBM_EINVAL;
     if (o.stop_rule == 1 && o.check_interval < 3) o.check_interval = 3;
     if (o.solo < 0 || o.solo > 2) return LBM_EINVAL;
+    if (o.schedule < 0 || o.schedule > 2) return LBM_EINVAL;
+    if (o.schedule == 2 && o.precision != LBM_FP32_SHIFTED) return LBM_EINVAL;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ENOMEM;
     b->n = n;
@@ -506,8 +943,14 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
             const std::string key = mask_key(d);
             auto it = tuned.find(key);
             if (it == tuned.end()) {
-                float best = INFINITY;
+                // With the stepwise schedule available, the layout is timed
+                // on the stepwise kernels (copies of the lattice filling the
+                // GPU) and units per thread on the persistent kernel, which
+                // still runs the chunks whose lattices do not fill the GPU.
+                const bool stepwise = o.precision == LBM_FP32_SHIFTED && o.schedule != 1;
+                float best = INFINITY, best_step = INFINITY;
                 int bl = LBM_LAYOUT_AA, bn = 1;
+                int bn_of[3] = {1, 1, 1};
                 for (int cl : {LBM_LAYOUT_AA, LBM_LAYOUT_SPARSE}) {
                     if (lay != -1 && cl != lay) continue;
                     lbm_options to = lo;
@@ -516,24 +959,42 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                     int rc = d.set >= 0 ? lbm_create(&c, d.mask, d.dims, d.set, d.tau, d.Lambda, d.force, &to)
                                         : lbm_create_rates(&c, d.mask, d.dims, d.s, d.force, &to);
                     if (rc != LBM_OK) return fail(rc);
+                    if (stepwise && o.solo != 2) {
+                        // timed as it will run: alone with its own kernels
+                        // when it fills the GPU, else in a group
+                        const int64_t un = cl == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+                        const bool alone = un >= kDirectUnits;
+                        if (alone) time_solo(b, c, 2);
+                        else time_candidate_step(b, c, 2);  // warm-up
+                        const float ms = alone ? time_solo(b, c, 8) : time_candidate_step(b, c, 8);
+                        if (ms < best_step) {
+                            best_step = ms;
+                            bl = cl;
+                        }
+                    }
+                    float best_here = INFINITY;
                     for (int cn : {1, 2}) {
                         if (np != 0 && cn != np) continue;
                         if (o.solo == 2) continue;
                         time_candidate(b, c, cn, 2);  // warm-up
                         const float ms = time_candidate(b, c, cn, 8);
-                        if (ms < best) {
+                        if (ms < best_here) {
+                            best_here = ms;
+                            bn_of[cl] = cn;
+                        }
+                        if (!stepwise && ms < best) {
                             best = ms;
                             bl = cl;
                             bn = cn;
                         }
                     }
-                    // a lattice that fills the GPU alone may run faster
-                    // without the batch (bn = 0: run it alone).  Only such
-                    // lattices are candidates: timed by itself a small lattice
-                    // pays every grid barrier alone, which in the batch is
-                    // shared by all lattices
+                    // Without the stepwise schedule, a lattice that fills the
+                    // GPU alone may run faster without the batch (bn = 0: run
+                    // it alone).  Only such lattices are candidates: timed by
+                    // itself a small lattice pays every grid barrier alone,
+                    // which in the batch is shared by all lattices
                     const int64_t units = cl == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
-                    if (np == 0 && (o.solo == 2 || (o.solo == 1 && units >= solo_min_units()))) {
+                    if (np == 0 && (o.solo == 2 || (o.solo == 1 && !stepwise && units >= solo_min_units()))) {
                         time_solo(b, c, 2);  // warm-up
                         const float ms = time_solo(b, c, 8);
                         if (ms < best || o.solo == 2) {
@@ -544,6 +1005,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                     }
                     lbm_destroy(c);
                 }
+                if (stepwise && o.solo != 2) bn = bn_of[bl];
                 it = tuned.emplace(key, std::make_pair(bl, bn)).first;
             }
             if (lay == -1) lay = it->second.first;
@@ -562,11 +1024,21 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     }
     std::vector<BatchLat> lats(n);
     int total_tiles = 0;
+    size_t step_tiles = 0;
+    uint32_t ngroups = 0;
     for (int i = 0; i < n; ++i) {
         lats[i] = make_lat(b->ctx[i], b->solo[i] ? 1 : b->npt[i]);
+        lats[i].goff = ngroups;
+        b->goff.push_back(ngroups);
+        ngroups += groups_of(lats[i]);
         if (!b->solo[i]) total_tiles += ntiles_of(lats[i]);
+        std::vector<Tile> ev, od;
+        step_tiles_of(lats[i], i, ev, od);
+        step_tiles += ev.size() + od.size();
     }
     b->max_tiles = total_tiles > 0 ? total_tiles : 1;
+    b->ngroups = ngroups;
+    b->max_step_tiles = (int)(step_tiles > 0 ? step_tiles : 1);
 #define CKB(call)                                        \
     do {                                                 \
         cudaError_t e3 = (call);                         \
@@ -580,6 +1052,11 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     CKB(cudaMalloc(&b->d_tile_part, sizeof(double) * 18 * (size_t)b->max_tiles));
     CKB(cudaMalloc(&b->d_bar, sizeof(GridBar)));
     CKB(cudaMalloc(&b->d_U, sizeof(double) * 9 * n));
+    if (o.precision == LBM_FP32_SHIFTED && o.schedule != 1) {
+        CKB(cudaMalloc(&b->d_step_tiles, sizeof(Tile) * (size_t)b->max_step_tiles));
+        CKB(cudaMalloc(&b->d_step_part, sizeof(double) * 3 * 3 * (size_t)(ngroups > 0 ? ngroups : 1)));
+        CKB(cudaMalloc(&b->d_want, (size_t)n));
+    }
     CKB(cudaMallocHost(&b->h_steps, sizeof(int64_t) * n));
     CKB(cudaMallocHost(&b->h_U, sizeof(double) * 9 * n));
     CKB(cudaMallocHost(&b->h_err, sizeof(int)));
@@ -601,7 +1078,10 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
     if (!b || !(tol >= 0.0)) return LBM_EINVAL;
     if (b->failed) return LBM_ETIMEOUT;
     std::vector<BatchLat> lats(b->n);
-    for (int i = 0; i < b->n; ++i) lats[i] = make_lat(b->ctx[i], b->solo[i] ? 1 : b->npt[i]);
+    for (int i = 0; i < b->n; ++i) {
+        lats[i] = make_lat(b->ctx[i], b->solo[i] ? 1 : b->npt[i]);
+        lats[i].goff = b->goff[i];
+    }
     // every lattice starts a fresh stopping-rule run; lattices that run alone
     // are not in the persistent kernel's tile table
     int nsolo = 0;
@@ -621,17 +1101,33 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
         drive[i] = d;
     }
     const int64_t K = b->opt.check_interval;
-    bool dirty = true;
+    bool dirty = true, dirty_step = true;
     int nact = b->n - nsolo;
     while (nact > 0) {
         cudaError_t e;
-        if (dirty) {
+        int64_t active_units = 0;
+        for (int i = 0; i < b->n; ++i)
+            if (b->active[i]) active_units += lats[i].units;
+        const bool stepwise = b->d_step_tiles &&
+                              (b->opt.schedule == 2 || active_units >= stepwise_min_units(b));
+        if (stepwise) {
+            if (dirty_step) {
+                e = upload_step_tiles(b, lats);
+                if (e != cudaSuccess) return launch_error(e);
+                dirty_step = false;
+            }
+            e = enqueue_step_chunk(b);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return launch_error(e);
+            b->stepwise_chunks++;
+        }
+        if (!stepwise && dirty) {
             e = upload_tiles(b, lats);
             if (e != cudaSuccess) return launch_error(e);
             dirty = false;
         }
         for (int i = 0; i < b->n; ++i) b->h_steps[i] = b->ctx[i]->steps;
-        if (b->opt.use_graph && !b->gexec && !b->graph_ok) {
+        if (!stepwise && b->opt.use_graph && !b->gexec && !b->graph_ok) {
             // capture the chunk once; fall back to direct launches if the
             // cooperative launch cannot be captured
             cudaGraph_t g = nullptr;
@@ -647,21 +1143,27 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
             cudaGetLastError();  // clear a failed capture
             if (!b->graph_ok) b->opt.use_graph = 0;
         }
-        if (b->graph_ok)
-            e = cudaGraphLaunch(b->gexec, b->stream);
-        else
-            e = enqueue_chunk(b);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) return launch_error(e);
-        b->launches += 2;
+        if (!stepwise) {
+            if (b->graph_ok)
+                e = cudaGraphLaunch(b->gexec, b->stream);
+            else
+                e = enqueue_chunk(b);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return launch_error(e);
+            b->launches += 2;
+            b->persistent_chunks++;
+        }
         if (*b->h_err) {
             b->failed = true;
             return LBM_ETIMEOUT;
         }
+        std::vector<char> advanced(b->n, 0);  // stepped through their own chunk graphs
+        if (stepwise)
+            for (const int i : b->direct) advanced[i] = 1;
         for (int i = 0; i < b->n; ++i) {
             if (!b->active[i]) continue;
             lbm_ctx *c = b->ctx[i];
-            c->steps += K;
+            if (!advanced[i]) c->steps += K;
             b->steps[i] += K;
             // slots 0, 1 (and 2 under stop rule 1) of this chunk's last steps
             const double *u = b->h_U + 9 * i;
@@ -700,7 +1202,7 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
                 c->converged = st == LBM_OK;
                 c->has_conv = st != LBM_EUNSTABLE;
                 --nact;
-                dirty = true;
+                dirty = dirty_step = true;
             }
         }
     }
@@ -758,5 +1260,12 @@ lbm_ctx *lbm_batch_lattice(lbm_batch *b, int32_t i) {
 }
 
 int64_t lbm_batch_kernel_launches(const lbm_batch *b) { return b ? b->launches : -1; }
+
+int lbm_batch_schedule_counts(const lbm_batch *b, int64_t *stepwise, int64_t *persistent) {
+    if (!b) return LBM_EINVAL;
+    if (stepwise) *stepwise = b->stepwise_chunks;
+    if (persistent) *persistent = b->persistent_chunks;
+    return LBM_OK;
+}
 
 }  // extern "C"

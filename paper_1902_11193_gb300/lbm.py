@@ -55,7 +55,7 @@ class BatchOptions(C.Structure):
                 ("check_interval", C.c_int32), ("linear_eq", C.c_int32), ("max_steps", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
                 ("barrier_timeout_ms", C.c_int32), ("test_skip_block", C.c_int32),
-                ("stop_rule", C.c_int32), ("solo", C.c_int32)]
+                ("stop_rule", C.c_int32), ("solo", C.c_int32), ("schedule", C.c_int32)]
 
 
 class Options(C.Structure):
@@ -119,6 +119,7 @@ def lib():
             "lbm_batch_config": (C.c_int, [vp, vp, vp]),
             "lbm_batch_lattice": (vp, [vp, i32]),
             "lbm_batch_kernel_launches": (i64, [vp]),
+            "lbm_batch_schedule_counts": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64)]),
             "lbm_batch_destroy": (None, [vp]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_last_cuda_error": (C.c_char_p, []),
@@ -366,12 +367,14 @@ class LBMBatch:
     set_/tau/Lambda or rates_, and force.  layout None lets the autotuner pick
     dense AA or sparse per distinct image; nodes_per_thread 0 likewise, and
     then a lattice may run alone with the single-lattice kernels where that is
-    faster (solo "auto"; "never", or "always" for every autotuned lattice)."""
+    faster (solo "auto"; "never", or "always" for every autotuned lattice).
+    schedule: "auto" (stepwise launches while the active lattices fill the
+    GPU, the persistent kernel below that), "persistent" or "stepwise"."""
 
     def __init__(self, lattices, precision="fp32", layout=None, nodes_per_thread=0,
                  check_interval=100, linear_eq=False, max_steps=1_000_000, stream=None,
                  use_graph=True, barrier_timeout_ms=2000, test_skip_block=-1, stop_rule=0,
-                 solo="auto"):
+                 solo="auto", schedule="auto"):
         self.masks = [np.ascontiguousarray(l["mask"], np.uint8) for l in lattices]
         n = len(lattices)
         descs = (LatticeDesc * n)()
@@ -404,6 +407,7 @@ class LBMBatch:
         o.test_skip_block = int(test_skip_block)
         o.stop_rule = int(stop_rule)
         o.solo = {"never": 0, "auto": 1, "always": 2}[solo]
+        o.schedule = {"auto": 0, "persistent": 1, "stepwise": 2}[schedule]
         if stream is not None:
             o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         h = C.c_void_p()
@@ -450,6 +454,13 @@ class LBMBatch:
     @property
     def kernel_launches(self) -> int:
         return int(lib().lbm_batch_kernel_launches(self._h))
+
+    def schedule_counts(self):
+        """(stepwise chunks, persistent chunks) run so far."""
+        a, b = C.c_int64(0), C.c_int64(0)
+        _check(lib().lbm_batch_schedule_counts(self._h, C.byref(a), C.byref(b)),
+               "lbm_batch_schedule_counts")
+        return int(a.value), int(b.value)
 
     def lattice(self, i: int) -> "LBMSolver":
         """Non-owning view of lattice i as a single-lattice solver."""

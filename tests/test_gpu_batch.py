@@ -1,4 +1,6 @@
-"""The batched persistent sweep against single-lattice runs and the oracle.
+"""The batched sweep against single-lattice runs and the oracle, under both
+schedules: the persistent kernel with grid barriers and the stepwise one
+(per step, one launch per class of lattices).
 
 Every batch member runs the same per-unit update on the same locations as a
 lattice run alone, and the stopping rule is evaluated on the same schedule,
@@ -96,7 +98,8 @@ def test_batch_retires_unstable_and_capped(L, geom):
 def test_batch_barrier_timeout_is_reported(L, geom):
     lats = _lattices(geom)
     B = L.LBMBatch(lats, precision="fp32", layout="aa", check_interval=10,
-                   barrier_timeout_ms=200, test_skip_block=0, solo="never")
+                   barrier_timeout_ms=200, test_skip_block=0, solo="never",
+                   schedule="persistent")
     rc = B.run(1e-7, raise_on_failure=False)
     assert rc == -6  # LBM_ETIMEOUT: the waits ran out, the kernel returned
     assert B.run(1e-7, raise_on_failure=False) == -6
@@ -105,3 +108,64 @@ def test_batch_barrier_timeout_is_reported(L, geom):
     C2 = L.LBMBatch(lats[:2], precision="fp32", layout="aa", check_interval=10, solo="never")
     steps, status = C2.run(1e-7)
     assert np.all(status == 0)
+
+
+@pytest.mark.parametrize("layout,rule", [("aa", 0), ("sparse", 1), (None, 0), (None, 1)])
+def test_batch_stepwise_bitwise_equals_single_runs(L, geom, layout, rule):
+    """The stepwise schedule: every chunk launched per step and class; the
+    members' step counts, populations and converged k bitwise those of lone
+    runs (two collision forms, both parities of the tile lists, ragged
+    tiles)."""
+    lats = _lattices(geom)
+    B = L.LBMBatch(lats, precision="fp32", layout=layout, check_interval=20, max_steps=6000,
+                   stop_rule=rule, schedule="stepwise")
+    steps, status = B.run(1e-7)
+    sw, pe = B.schedule_counts()
+    assert sw > 0 and pe == 0
+    lay, _ = B.config()
+    kb = B.permeability()
+    for i, l in enumerate(lats):
+        S = L.LBMSolver(l["mask"], l["set_"], l["tau"], l.get("Lambda", 3 / 16), l["force"],
+                        precision="fp32", layout=["ab", "aa", "sparse"][lay[i]],
+                        check_interval=20, max_steps=6000, stop_rule=rule)
+        rc, st = S.run_to_convergence(1e-7)
+        assert rc == status[i] and st == steps[i]
+        assert np.array_equal(S.get_populations(), B.lattice(i).get_populations())
+        assert np.array_equal(S.converged_permeability(), kb[i], equal_nan=True)
+        S.close()
+
+
+def test_batch_schedule_switches_midway(L, geom):
+    """Two large lattices keep the active units above the stepwise threshold
+    for the first chunk; without a drive they meet the stopping rule at
+    their first check and retire, and the small slow ones (tau = 0.6)
+    finish under the persistent kernel.  Every member still equals its lone
+    run bitwise."""
+    big = geom.sphere_array(96, "sc", c=0.1)
+    lats = [dict(mask=big, set_="B", tau=1.6, force=(0, 0, 0)),
+            dict(mask=big, set_="D", tau=1.6, force=(0, 0, 0))]
+    lats += [dict(l, tau=0.6) for l in _lattices(geom)[:3]]
+    B = L.LBMBatch(lats, precision="fp32", layout="sparse", check_interval=50, max_steps=20000)
+    steps, status = B.run(1e-6)
+    sw, pe = B.schedule_counts()
+    assert sw > 0 and pe > 0, (sw, pe)
+    kb = B.permeability()
+    for i, l in enumerate(lats):
+        S = L.LBMSolver(l["mask"], l["set_"], l["tau"], l.get("Lambda", 3 / 16), l["force"],
+                        precision="fp32", layout="sparse", check_interval=50, max_steps=20000)
+        rc, st = S.run_to_convergence(1e-6)
+        assert rc == status[i] and st == steps[i]
+        assert np.array_equal(S.get_populations(), B.lattice(i).get_populations())
+        assert np.array_equal(S.converged_permeability(), kb[i], equal_nan=True)
+        S.close()
+
+
+def test_batch_stepwise_retires_unstable(L, geom):
+    lats = _lattices(geom)[:2]
+    lats.append(dict(mask=geom.sphere_array(16, "sc", c=0.2), set_="SRT", tau=0.5001,
+                     force=(0.5, 0, 0)))
+    B = L.LBMBatch(lats, precision="fp32", layout="sparse", check_interval=10, max_steps=300,
+                   schedule="stepwise")
+    steps, status = B.run(0.0)
+    assert status[2] == -5
+    assert status[0] == -4 and status[1] == -4 and steps[0] == 300
