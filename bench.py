@@ -585,10 +585,13 @@ def sweep_run(args, stream):
     t2 = time.perf_counter()
     lay, npt = B.config()
     blaunch = B.kernel_launches
+    chunks = B.schedule_counts()
     B.close()
     t3 = time.perf_counter()
     ks, seq_launches, seq_steps = [], 0, []
+    by_edge = {}
     for l, layout in zip(lats, lay):
+        ts = time.perf_counter()
         S = lbm.LBMSolver(l["mask"], l["set_"], l["tau"], l["Lambda"], l["force"],
                           precision="fp32", layout=["ab", "aa", "sparse"][layout],
                           check_interval=K, max_steps=200000, stream=stream)
@@ -597,6 +600,8 @@ def sweep_run(args, stream):
         seq_launches += S.kernel_launches
         seq_steps.append(st)
         S.close()
+        e = str(l["mask"].shape[0])
+        by_edge[e] = by_edge.get(e, 0.0) + time.perf_counter() - ts
     torch.cuda.synchronize()
     t4 = time.perf_counter()
     fluid = np.array([int((l["mask"] == 0).sum()) for l in lats])
@@ -612,7 +617,9 @@ def sweep_run(args, stream):
             "max_k_diff": float(np.max(np.abs(np.array(ks)[:, 0] - kb[:, 0]))),  # driven (x) component
             "k_bitwise_equal": bool(np.array_equal(np.array(ks)[:, 0], kb[:, 0])),
             "layouts": {"aa": int(np.sum(lay == 1)), "sparse": int(np.sum(lay == 2)),
-                        "npt2": int(np.sum(npt == 2)), "alone": int(np.sum(npt == 0))}}
+                        "npt2": int(np.sum(npt == 2)), "alone": int(np.sum(npt == 0))},
+            "chunks": {"stepwise": chunks[0], "persistent": chunks[1]},
+            "sequential_s_by_edge": by_edge}
 
 
 ADJOINT_SETS = (("B", 3 / 16), ("D", 3 / 16), ("E", 3 / 16), ("E", 3 / 8))
