@@ -29,6 +29,10 @@
 
 #include "lbm_step.cuh"
 
+#ifndef LBM_ADJ_LEAN
+#define LBM_ADJ_LEAN 1  // 0: the FP32 sparse adjoint through the general index path
+#endif
+
 namespace lbm {
 
 // Same unit machinery as the state readers (lbm_kernels.cu).
@@ -38,6 +42,7 @@ struct AdjView {
     const uint32_t *lw;
     SparseMap sm;
     Dims d;
+    OddMap om;  // sparse, Lx < 2^13: the odd step's lean index tables (om.rec null otherwise)
     // bounds-check build: a location outside the 19 * units slots
     __device__ __forceinline__ bool ok(size_t at) const { return in_range(at, (uint64_t)Q * units, sm.flag); }
 };
@@ -263,8 +268,11 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
 // slower here.
 // CHK: a checking launch (residual partials); its own instantiation, so
 // that the plain launches carry none of its registers.
-template <typename T, bool FROM_H, bool SP, bool CHK>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
+#ifndef LBM_ADJ_LEAN_MIN_BLOCKS
+#define LBM_ADJ_LEAN_MIN_BLOCKS 5  // 48 registers (8-B spill): 3% faster than four
+#endif
+template <typename T, bool FROM_H, bool SP, bool CHK, bool LEAN = false>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : (LEAN ? LBM_ADJ_LEAN_MIN_BLOCKS : 4))
     k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in, T *__restrict__ psi_out,
                AdjView v, Collide<T> p, T coef, int d, double *partials) {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,7 +282,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : 4)
         bool fluid = true;
         // population i of x went downstream to x + c_i = x - c_opp(i), or
         // bounced back into slot opp(i) of x
-        if (SP) {
+        if (SP && LEAN) {
+            // the forward odd step's location of direction opp(i) is slot i
+            // of the node at x + c_i, or slot opp(i) of x where that voxel is
+            // solid: exactly where psi_i(x + c_i) (or the bounceback value)
+            // sits in the two-array layout
+            uint32_t loc[Q];
+            odd_lean_locations(v.om, u, __ldg(v.om.rec + u), loc);
+            phi[0] = psi_in[u];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const uint32_t at = loc[opp(i)];
+                phi[i] = v.ok(at) ? psi_in[at] : T(0);
+            }
+        } else if (SP) {
             SparseNode sn;
             sn.init(u, v.sm);
             phi[0] = psi_in[u];
@@ -391,6 +412,16 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
     const unsigned grid = adj_step_grid(v.units);
     if (grid == 0) return;
     const bool sp = v.layout == LBM_LAYOUT_SPARSE;
+    if (LBM_ADJ_LEAN && sp && v.om.rec && sizeof(T) == 4) {  // the lean index path (FP32)
+        if (partials)
+            k_adj_step<T, FROM_H, true, true, true><<<grid, 256, 0, c->stream>>>(
+                H, psi_in, psi_out, v, p, coef, d, partials);
+        else
+            k_adj_step<T, FROM_H, true, false, true><<<grid, 256, 0, c->stream>>>(
+                H, psi_in, psi_out, v, p, coef, d, nullptr);
+        c->launches++;
+        return;
+    }
     if (partials) {
         if (sp)
             k_adj_step<T, FROM_H, true, true><<<grid, 256, 0, c->stream>>>(H, psi_in, psi_out, v, p,
@@ -420,7 +451,7 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
 // ACC: add the block's sums into `partials` (the transient sweep keeps one
 // accumulator per block over all its steps).
 // SP: sparse layout (else dense), as in k_adj_step.
-template <typename T, bool ACC, bool SP>
+template <typename T, bool ACC, bool SP, bool LEAN = false>
 __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const T *__restrict__ psi_a,
                                                   const T *__restrict__ psi_b, AdjView v,
                                                   Collide<T> p, int d, double *partials) {
@@ -439,7 +470,13 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
         bool fluid = true;
         T phi[Q];
         // the value streamed back to u from direction i, as k_adj_step reads it
-        if (SP) {
+        if (SP && LEAN) {
+            uint32_t loc[Q];
+            odd_lean_locations(v.om, u, __ldg(v.om.rec + u), loc);
+            phi[0] = psi_at(u);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) phi[i] = psi_at(loc[opp(i)]);
+        } else if (SP) {
             SparseNode sn;
             sn.init(u, v.sm);
             phi[0] = psi_at(u);
@@ -516,7 +553,9 @@ __global__ void __launch_bounds__(256) k_adj_grad(const T *__restrict__ H, const
 template <typename T, bool ACC>
 void launch_adj_grad(lbm_ctx *c, const AdjView &v, unsigned grid, const T *H, const T *psi_a,
                      const T *psi_b, const Collide<T> &p, int d, double *partials) {
-    if (v.layout == LBM_LAYOUT_SPARSE)
+    if (LBM_ADJ_LEAN && v.layout == LBM_LAYOUT_SPARSE && v.om.rec && sizeof(T) == 4)
+        k_adj_grad<T, ACC, true, true><<<grid, 256, 0, c->stream>>>(H, psi_a, psi_b, v, p, d, partials);
+    else if (v.layout == LBM_LAYOUT_SPARSE)
         k_adj_grad<T, ACC, true><<<grid, 256, 0, c->stream>>>(H, psi_a, psi_b, v, p, d, partials);
     else
         k_adj_grad<T, ACC, false><<<grid, 256, 0, c->stream>>>(H, psi_a, psi_b, v, p, d, partials);
@@ -546,6 +585,7 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict_
 }
 
 SparseMap sparse_map(const lbm_ctx *c);
+OddMap odd_map(const lbm_ctx *c);
 
 static AdjView make_adj_view(const lbm_ctx *c) {
     AdjView v;
@@ -554,6 +594,7 @@ static AdjView make_adj_view(const lbm_ctx *c) {
     v.lw = c->d_lw;
     v.sm = sparse_map(c);
     v.d = Dims{c->Lx, c->Ly, c->Lz, (uint32_t)c->N};
+    v.om = odd_map(c);  // rec is null unless the sparse layout built the lean tables
     return v;
 }
 

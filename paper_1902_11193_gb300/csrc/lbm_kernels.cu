@@ -536,7 +536,7 @@ static inline bool narrow_index(const lbm_ctx *c) {
 }
 
 // The kernel parameters of k_sparse_odd_l (see OddMap).
-static OddMap odd_map(const lbm_ctx *c) {
+OddMap odd_map(const lbm_ctx *c) {
     OddMap o;
     memset(&o, 0, sizeof o);
     o.rec = c->d_orec;
