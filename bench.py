@@ -54,6 +54,11 @@ def parse():
     p.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     p.add_argument("--adjoint-size", type=int, default=128,
                    help="edge of the adjoint leg's Boolean medium (r = 6, porosity 0.35)")
+    p.add_argument("--adjoint-sets", default="B,D,E3/16,E3/8",
+                   help="rate sets of the adjoint grid (E with its magic parameter)")
+    p.add_argument("--adjoint-taus", default="0.8,1.0,1.3", help="taus of the adjoint grid")
+    p.add_argument("--no-transient", action="store_true",
+                   help="skip the transient adjoint of the adjoint leg")
     p.add_argument("--large", action="store_true", default=True,
                    help="1024^3 low-porosity sparse leg, FP32 vs FP16 storage")
     p.add_argument("--no-large", dest="large", action="store_false")
@@ -622,10 +627,6 @@ def sweep_run(args, stream):
             "sequential_s_by_edge": by_edge}
 
 
-ADJOINT_SETS = (("B", 3 / 16), ("D", 3 / 16), ("E", 3 / 16), ("E", 3 / 8))
-ADJOINT_TAUS = (0.8, 1.0, 1.3)
-
-
 def adjoint_grads(S, g, set_, lam, tau, F):
     """Normalised gradients theta (dk/dtheta) / k of one steady adjoint."""
     k = g["k"]
@@ -655,13 +656,21 @@ def adjoint_run(args, stream):
     mask, _ = geometry.boolean(L, 6, 0.35, seed=1902_11193 + 4)
     nf = int((mask == 0).sum())
     res = {"workload": f"boolean-{L}^3 r=6 porosity=0.35, F=1e-6 x, fp32 sparse, two-step-mean "
-                       "stopping rule (tol 1e-8), adjoint tol 1e-6; Sets B, D, E(3/16), E(3/8) "
-                       "x tau 0.8, 1.0, 1.3", "grid": []}
+                       "stopping rule (tol 1e-8), adjoint tol 1e-6; sets "
+                       f"{args.adjoint_sets} x tau {args.adjoint_taus}", "grid": []}
     steps_d1 = None
     t_fwd = t_adj = 0.0
     iters = 0
-    for set_, lam in ADJOINT_SETS:
-        for tau in ADJOINT_TAUS:
+    sets = []
+    for tok in args.adjoint_sets.split(","):
+        if tok.startswith("E"):
+            num, den = tok[1:].split("/")
+            sets.append(("E", float(num) / float(den)))
+        else:
+            sets.append((tok, 3 / 16))
+    taus = tuple(float(t) for t in args.adjoint_taus.split(","))
+    for set_, lam in sets:
+        for tau in taus:
             S = lbm.LBMSolver(mask, set_, tau, lam, force=(F, 0, 0), precision="fp32",
                               layout="sparse", check_interval=100, stream=stream, stop_rule=1,
                               max_steps=400000)
@@ -687,7 +696,7 @@ def adjoint_run(args, stream):
     res["forward_s_total"] = t_fwd
     res["adjoint_s_total"] = t_adj
     res["adjoint_fluid_MLUPS"] = nf * iters / t_adj / 1e6 if t_adj > 0 else None
-    if steps_d1 is None:
+    if steps_d1 is None or args.no_transient:
         return res
     # transient adjoint: the gradient of k after the same number of steps
     # from rest, by a checkpointed reverse sweep
