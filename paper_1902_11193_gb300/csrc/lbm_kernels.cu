@@ -255,6 +255,59 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// Even steps, FP16 storage: four nodes per thread, 256 apart, all 76 loads
+// issued before the first collision.  The stored halves of two nodes are
+// packed into one 32-bit register (half2), so the four nodes' loads fit the
+// registers the two-node FP32 kernel uses, and a warp keeps as many bytes
+// in flight as that kernel does (two-byte values need twice the loads).
+#ifndef LBM_EVEN_H4
+#define LBM_EVEN_H4 1  // 0: FP16 even steps through k_sparse_even_x2 as well
+#endif
+template <int K, bool RED>
+__global__ void __launch_bounds__(256, 2)
+    k_sparse_even_h4(__half *A, uint32_t Nf, Collide<float> p, float ld_scale, float st_scale,
+                     Reduce red) {
+    const uint32_t k0 = blockIdx.x * 1024u + threadIdx.x;
+    __half2 h01[Q], h23[Q];  // (node 0, node 1) and (node 2, node 3) of this thread
+    const __half z = __float2half_rn(0.f);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const __half *a = A + (uint32_t)j * Nf;
+        h01[j] = __halves2half2(k0 < Nf ? a[k0] : z, k0 + 256u < Nf ? a[k0 + 256u] : z);
+        h23[j] = __halves2half2(k0 + 512u < Nf ? a[k0 + 512u] : z,
+                                k0 + 768u < Nf ? a[k0 + 768u] : z);
+    }
+    __shared__ double wsum[RED ? 4 : 1][8][3];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t k = k0 + 256u * r;
+        const bool v = k < Nf;
+        float g[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const __half2 h = r < 2 ? h01[j] : h23[j];
+            g[j] = __fmul_rn(__half2float((r & 1) ? __high2half(h) : __low2half(h)), ld_scale);
+        }
+        float jx = 0.f, jy = 0.f, jz = 0.f;
+        if (v) {
+            collide_as<K, float>(g, p, jx, jy, jz);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) Store<__half>::st(A + (uint32_t)j * Nf + k, g[opp(j)], st_scale);
+        }
+        if (RED) warp_momentum_store<float>(jx, jy, jz, v, wsum[RED ? r : 0], red.flag);
+    }
+    if (RED) {  // partials 4b .. 4b + 3 (nodes 256 g .. 256 g + 255, as in k_sparse)
+        __syncthreads();
+        const uint32_t g0 = 4u * blockIdx.x;
+        int ng = 0;
+        while (ng < 4 && (g0 + (uint32_t)ng) * 256u < Nf) ++ng;
+        if ((int)threadIdx.x < 3 * ng) {
+            const int r = threadIdx.x / 3, a = threadIdx.x % 3;
+            red.partials[3 * (size_t)(g0 + (uint32_t)r) + a] = group_momentum_total(wsum[r], a);
+        }
+    }
+}
+
 // ------------------------------------------------------- reduction finalise
 
 // Fixed-order sum of the per-block partials: thread t adds blocks t, t+T, ...
@@ -604,6 +657,19 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
         if (grid == 0) break;
         // measuring steps write one partial per 256 fluid nodes
         const unsigned groups = (unsigned)((c->Nf + 255) / 256);
+        if constexpr (sizeof(S) == 2 && LBM_EVEN_H4) {
+            if (!odd && narrow_index(c)) {
+                const unsigned g4 = (unsigned)((c->Nf + 1023) / 1024);
+                if (reduce)
+                    k_sparse_even_h4<K, true><<<g4, 256, 0, c->stream>>>(
+                        (__half *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                else
+                    k_sparse_even_h4<K, false><<<g4, 256, 0, c->stream>>>(
+                        (__half *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                grid = reduce ? groups : g4;
+                break;
+            }
+        }
         if constexpr (sizeof(S) <= 4) {
             if (!odd && narrow_index(c)) {
                 const unsigned g2 = (unsigned)((c->Nf + 511) / 512);
