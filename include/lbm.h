@@ -342,15 +342,18 @@ typedef struct {
                                    (every autotuned lattice runs alone, whatever its
                                    size).  The stepwise schedule needs no lone runs, so
                                    with it the default offers none. */
-    int32_t schedule;           /* 0 (default): per chunk, the stepwise schedule while
-                                   the active lattices hold at least four waves of the
-                                   persistent kernel's threads (FP32), the persistent
-                                   kernel below that; 1: always the persistent kernel;
-                                   2: always stepwise (FP32 only).  Stepwise: per step,
-                                   one launch per class of lattices (layout x collision
-                                   form x parity) of the multi-lattice twins of the
-                                   single-lattice kernels; no grid barrier.  Results are
-                                   bitwise the same under either schedule. */
+    int32_t schedule;           /* 0 (default): per chunk, each lattice of at least 10^5
+                                   units (fluid nodes or voxels) runs the chunk with its
+                                   own single-lattice kernels, replayed from its own CUDA
+                                   graph, and all others share one persistent launch;
+                                   1: every lattice in the persistent kernel; 2: grouped
+                                   stepwise (FP32 only): per step, one launch per class
+                                   of lattices (layout x collision form x parity) of the
+                                   multi-lattice twins of the single-lattice kernels,
+                                   lattices packed into groups that fit L2, each group
+                                   run through the whole chunk in turn; lattices of at
+                                   least 10^5 units on their own kernels.  Results are
+                                   bitwise the same under every schedule. */
 } lbm_batch_options;
 
 typedef struct lbm_batch lbm_batch;
@@ -378,7 +381,8 @@ int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *nodes_per_thread);
 lbm_ctx *lbm_batch_lattice(lbm_batch *b, int32_t i);
 /* Kernel launches and graph replays so far (launch accounting). */
 int64_t lbm_batch_kernel_launches(const lbm_batch *b);
-/* Chunks run under each schedule so far (nullable outputs). */
+/* Chunks so far that ran lattices with their own kernels or grouped stepwise
+ * launches (stepwise), and chunks with a persistent launch (nullable). */
 int lbm_batch_schedule_counts(const lbm_batch *b, int64_t *stepwise, int64_t *persistent);
 void lbm_batch_destroy(lbm_batch *b);
 

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_adj_j3(const T *__restrict__ H, AdjView
 // the node's own slots, so those captures need no index data; odd parity
 // uses the interior upstream formulas with the x faces redone, as the
 // adjoint step does.
-template <typename S, bool SP>
+template <typename S, bool SP, bool LEAN = false>
 __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjState st,
                                                      float ld_scale, typename Store<S>::C *H,
                                                      int average) {
@@ -212,6 +212,14 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
         if (st.parity == 0) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) val[i] = (C)Store<S>::ld(A + (size_t)i * v.units + u, ld_scale);
+        } else if (LEAN) {
+            // the streamed value of direction i is where the forward odd step
+            // of u reads it
+            uint32_t loc[Q];
+            odd_lean_locations(v.om, u, __ldg(v.om.rec + u), loc);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                val[i] = v.ok(loc[i]) ? (C)Store<S>::ld(A + loc[i], ld_scale) : C(0);
         } else {
             SparseNode sn;
             sn.init(u, v.sm);
@@ -621,7 +629,10 @@ static void capture(lbm_ctx *c, const AdjView &v, unsigned grid, T *H, int avera
                                                                       (double *)H, average);
         break;
     case LBM_FP32_SHIFTED:
-        if (sp)
+        if (sp && v.om.rec && LBM_ADJ_LEAN)
+            k_adj_capture<float, true, true><<<grid, 256, 0, c->stream>>>((const float *)A, v, st,
+                                                                          lds, (float *)H, average);
+        else if (sp)
             k_adj_capture<float, true><<<grid, 256, 0, c->stream>>>((const float *)A, v, st, lds,
                                                                     (float *)H, average);
         else
@@ -629,7 +640,10 @@ static void capture(lbm_ctx *c, const AdjView &v, unsigned grid, T *H, int avera
                                                                      (float *)H, average);
         break;
     default:
-        if (sp)
+        if (sp && v.om.rec && LBM_ADJ_LEAN)
+            k_adj_capture<__half, true, true><<<grid, 256, 0, c->stream>>>(
+                (const __half *)A, v, st, lds, (float *)H, average);
+        else if (sp)
             k_adj_capture<__half, true><<<grid, 256, 0, c->stream>>>((const __half *)A, v, st, lds,
                                                                      (float *)H, average);
         else

@@ -430,6 +430,7 @@ struct lbm_batch {
     std::vector<StepClass> classes;
     std::vector<int> group_end;  // classes of group g: [group_end[g-1], group_end[g])
     std::vector<int> direct;     // active lattices stepped with their own kernels
+    std::vector<char> in_direct;  // automatic schedule: left out of the persistent launch
     Tile *d_step_tiles;
     int max_step_tiles;
     double *d_step_part;
@@ -566,13 +567,14 @@ size_t lat_bytes(const lbm_batch *b, const BatchLat &L) {
     return (size_t)L.units * (Q * elem + (L.layout == LBM_LAYOUT_SPARSE ? 8 : 4));
 }
 
-// A lattice with at least this many units fills the GPU by itself: under the
-// stepwise schedule it runs each chunk with its own single-lattice kernels
-// (whose parameters sit in the constant bank; at 96^3 they stepped 40%
-// faster than the multi-lattice kernels with one lattice per launch), on
-// the batch's stream, its chunk replayed from its own CUDA graph.
+// A lattice with at least this many units fills the GPU by itself: it runs
+// each chunk with its own single-lattice kernels (whose parameters sit in
+// the constant bank; at 96^3 they stepped 40% faster than the multi-lattice
+// kernels with one lattice per launch), on the batch's stream, its chunk
+// replayed from its own CUDA graph, its state staying in L2 from step to
+// step where it fits.
 #ifndef LBM_STEP_DIRECT_UNITS
-#define LBM_STEP_DIRECT_UNITS 300000
+#define LBM_STEP_DIRECT_UNITS 100000
 #endif
 constexpr int64_t kDirectUnits = LBM_STEP_DIRECT_UNITS;
 
@@ -758,7 +760,7 @@ cudaError_t upload_tiles(lbm_batch *b, const std::vector<BatchLat> &lats) {
     std::vector<Tile> tiles;
     std::vector<int2> ranges(b->n, make_int2(0, 0));
     for (int i = 0; i < b->n; ++i) {
-        if (!b->active[i]) continue;
+        if (!b->active[i] || (i < (int)b->in_direct.size() && b->in_direct[i])) continue;
         const int nt = ntiles_of(lats[i]);
         ranges[i] = make_int2((int)tiles.size(), nt);
         for (int t = 0; t < nt; ++t) tiles.push_back(Tile{i, (uint32_t)t * kTileThreads * lats[i].npt});
@@ -943,11 +945,13 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
             const std::string key = mask_key(d);
             auto it = tuned.find(key);
             if (it == tuned.end()) {
-                // With the stepwise schedule available, the layout is timed
-                // on the stepwise kernels (copies of the lattice filling the
-                // GPU) and units per thread on the persistent kernel, which
-                // still runs the chunks whose lattices do not fill the GPU.
-                const bool stepwise = o.precision == LBM_FP32_SHIFTED && o.schedule != 1;
+                // Each candidate layout is timed as it will run: under the
+                // automatic schedule, alone with its own kernels where it
+                // fills the GPU, else in the persistent kernel; under the
+                // grouped stepwise schedule, on the stepwise kernels (copies
+                // of the lattice filling the GPU).  Units per thread are
+                // timed on the persistent kernel.
+                const bool stepwise = o.schedule != 1;
                 float best = INFINITY, best_step = INFINITY;
                 int bl = LBM_LAYOUT_AA, bn = 1;
                 int bn_of[3] = {1, 1, 1};
@@ -959,19 +963,8 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                     int rc = d.set >= 0 ? lbm_create(&c, d.mask, d.dims, d.set, d.tau, d.Lambda, d.force, &to)
                                         : lbm_create_rates(&c, d.mask, d.dims, d.s, d.force, &to);
                     if (rc != LBM_OK) return fail(rc);
-                    if (stepwise && o.solo != 2) {
-                        // timed as it will run: alone with its own kernels
-                        // when it fills the GPU, else in a group
-                        const int64_t un = cl == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
-                        const bool alone = un >= kDirectUnits;
-                        if (alone) time_solo(b, c, 2);
-                        else time_candidate_step(b, c, 2);  // warm-up
-                        const float ms = alone ? time_solo(b, c, 8) : time_candidate_step(b, c, 8);
-                        if (ms < best_step) {
-                            best_step = ms;
-                            bl = cl;
-                        }
-                    }
+                    const int64_t un = cl == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+                    const bool alone = un >= kDirectUnits;
                     float best_here = INFINITY;
                     for (int cn : {1, 2}) {
                         if (np != 0 && cn != np) continue;
@@ -986,6 +979,22 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                             best = ms;
                             bl = cl;
                             bn = cn;
+                        }
+                    }
+                    if (stepwise && o.solo != 2) {
+                        float ms;
+                        if (alone) {
+                            time_solo(b, c, 2);  // warm-up
+                            ms = time_solo(b, c, 8);
+                        } else if (o.schedule == 2 && o.precision == LBM_FP32_SHIFTED) {
+                            time_candidate_step(b, c, 2);
+                            ms = time_candidate_step(b, c, 8);
+                        } else {
+                            ms = best_here;  // the persistent kernel's time
+                        }
+                        if (ms < best_step) {
+                            best_step = ms;
+                            bl = cl;
                         }
                     }
                     // Without the stepwise schedule, a lattice that fills the
@@ -1052,7 +1061,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     CKB(cudaMalloc(&b->d_tile_part, sizeof(double) * 18 * (size_t)b->max_tiles));
     CKB(cudaMalloc(&b->d_bar, sizeof(GridBar)));
     CKB(cudaMalloc(&b->d_U, sizeof(double) * 9 * n));
-    if (o.precision == LBM_FP32_SHIFTED && o.schedule != 1) {
+    if (o.precision == LBM_FP32_SHIFTED && o.schedule == 2) {
         CKB(cudaMalloc(&b->d_step_tiles, sizeof(Tile) * (size_t)b->max_step_tiles));
         CKB(cudaMalloc(&b->d_step_part, sizeof(double) * 3 * 3 * (size_t)(ngroups > 0 ? ngroups : 1)));
         CKB(cudaMalloc(&b->d_want, (size_t)n));
@@ -1105,11 +1114,16 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
     int nact = b->n - nsolo;
     while (nact > 0) {
         cudaError_t e;
-        int64_t active_units = 0;
-        for (int i = 0; i < b->n; ++i)
-            if (b->active[i]) active_units += lats[i].units;
-        const bool stepwise = b->d_step_tiles &&
-                              (b->opt.schedule == 2 || active_units >= stepwise_min_units(b));
+        // schedule 2: grouped multi-lattice launches per step.  Otherwise,
+        // under the automatic schedule, lattices that fill the GPU alone run
+        // their chunks with their own single-lattice kernels (graph-replayed)
+        // and all others share one persistent launch; schedule 1 puts every
+        // lattice in the persistent launch.
+        const bool stepwise = b->d_step_tiles && b->opt.schedule == 2;
+        std::vector<int> direct_now;
+        if (!stepwise && b->opt.schedule == 0)
+            for (int i = 0; i < b->n; ++i)
+                if (b->active[i] && (int64_t)lats[i].units >= kDirectUnits) direct_now.push_back(i);
         if (stepwise) {
             if (dirty_step) {
                 e = upload_step_tiles(b, lats);
@@ -1120,38 +1134,59 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
             if (e != cudaSuccess) return launch_error(e);
             b->stepwise_chunks++;
-        }
-        if (!stepwise && dirty) {
-            e = upload_tiles(b, lats);
-            if (e != cudaSuccess) return launch_error(e);
-            dirty = false;
-        }
-        for (int i = 0; i < b->n; ++i) b->h_steps[i] = b->ctx[i]->steps;
-        if (!stepwise && b->opt.use_graph && !b->gexec && !b->graph_ok) {
-            // capture the chunk once; fall back to direct launches if the
-            // cooperative launch cannot be captured
-            cudaGraph_t g = nullptr;
-            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                cudaError_t ec = enqueue_chunk(b);
-                e = cudaStreamEndCapture(b->stream, &g);
-                if (ec == cudaSuccess && e == cudaSuccess &&
-                    cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess)
-                    b->graph_ok = true;
-                if (g) cudaGraphDestroy(g);
+        } else {
+            for (const int i : direct_now) {
+                lbm_ctx *c = b->ctx[i];
+                const int64_t l0 = c->launches;
+                if (enqueue_measured_chunk(c, K - (b->opt.stop_rule == 1 ? 3 : 2),
+                                           b->opt.stop_rule == 1 ? 3 : 2) != LBM_OK)
+                    return LBM_ECUDA;
+                b->launches += c->launches - l0;
             }
-            cudaGetLastError();  // clear a failed capture
-            if (!b->graph_ok) b->opt.use_graph = 0;
-        }
-        if (!stepwise) {
-            if (b->graph_ok)
-                e = cudaGraphLaunch(b->gexec, b->stream);
-            else
-                e = enqueue_chunk(b);
+            if (!direct_now.empty()) b->stepwise_chunks++;
+            if ((int)direct_now.size() < nact) {
+                if (dirty) {
+                    b->in_direct.assign(b->n, 0);
+                    for (const int i : direct_now) b->in_direct[i] = 1;
+                    e = upload_tiles(b, lats);
+                    if (e != cudaSuccess) return launch_error(e);
+                    dirty = false;
+                }
+                for (int i = 0; i < b->n; ++i) b->h_steps[i] = b->ctx[i]->steps;
+                if (b->opt.use_graph && !b->gexec && !b->graph_ok) {
+                    // capture the chunk once; fall back to direct launches if
+                    // the cooperative launch cannot be captured
+                    cudaGraph_t g = nullptr;
+                    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                    if (e == cudaSuccess) {
+                        cudaError_t ec = enqueue_chunk(b);
+                        e = cudaStreamEndCapture(b->stream, &g);
+                        if (ec == cudaSuccess && e == cudaSuccess &&
+                            cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess)
+                            b->graph_ok = true;
+                        if (g) cudaGraphDestroy(g);
+                    }
+                    cudaGetLastError();  // clear a failed capture
+                    if (!b->graph_ok) b->opt.use_graph = 0;
+                }
+                if (b->graph_ok)
+                    e = cudaGraphLaunch(b->gexec, b->stream);
+                else
+                    e = enqueue_chunk(b);
+                if (e != cudaSuccess) return launch_error(e);
+                b->launches += 2;
+                b->persistent_chunks++;
+            } else {
+                *b->h_err = 0;
+            }
+            const int nmeas = b->opt.stop_rule == 1 ? 3 : 2;
+            for (const int i : direct_now)  // their slots, after the persistent chunk's copy
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->h_U + 9 * (size_t)i, b->ctx[i]->d_U,
+                                        sizeof(double) * 3 * nmeas, cudaMemcpyDeviceToHost,
+                                        b->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
             if (e != cudaSuccess) return launch_error(e);
-            b->launches += 2;
-            b->persistent_chunks++;
         }
         if (*b->h_err) {
             b->failed = true;
@@ -1160,6 +1195,7 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
         std::vector<char> advanced(b->n, 0);  // stepped through their own chunk graphs
         if (stepwise)
             for (const int i : b->direct) advanced[i] = 1;
+        for (const int i : direct_now) advanced[i] = 1;
         for (int i = 0; i < b->n; ++i) {
             if (!b->active[i]) continue;
             lbm_ctx *c = b->ctx[i];

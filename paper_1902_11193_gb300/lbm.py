@@ -368,8 +368,9 @@ class LBMBatch:
     dense AA or sparse per distinct image; nodes_per_thread 0 likewise, and
     then a lattice may run alone with the single-lattice kernels where that is
     faster (solo "auto"; "never", or "always" for every autotuned lattice).
-    schedule: "auto" (stepwise launches while the active lattices fill the
-    GPU, the persistent kernel below that), "persistent" or "stepwise"."""
+    schedule: "auto" (lattices of at least 10^5 units on their own
+    graph-replayed kernels, the rest in one persistent launch),
+    "persistent", or "stepwise" (grouped multi-lattice launches per step)."""
 
     def __init__(self, lattices, precision="fp32", layout=None, nodes_per_thread=0,
                  check_interval=100, linear_eq=False, max_steps=1_000_000, stream=None,

@@ -136,11 +136,11 @@ def test_batch_stepwise_bitwise_equals_single_runs(L, geom, layout, rule):
 
 
 def test_batch_schedule_switches_midway(L, geom):
-    """Two large lattices keep the active units above the stepwise threshold
-    for the first chunk; without a drive they meet the stopping rule at
-    their first check and retire, and the small slow ones (tau = 0.6)
-    finish under the persistent kernel.  Every member still equals its lone
-    run bitwise."""
+    """Two large lattices (over 10^5 units) run their first chunk with their
+    own kernels beside the small ones' persistent launch; without a drive
+    they meet the stopping rule at their first check and retire, and the
+    small slow ones (tau = 0.6) finish in the persistent kernel alone.  Every
+    member still equals its lone run bitwise."""
     big = geom.sphere_array(96, "sc", c=0.1)
     lats = [dict(mask=big, set_="B", tau=1.6, force=(0, 0, 0)),
             dict(mask=big, set_="D", tau=1.6, force=(0, 0, 0))]
@@ -169,3 +169,30 @@ def test_batch_stepwise_retires_unstable(L, geom):
     steps, status = B.run(0.0)
     assert status[2] == -5
     assert status[0] == -4 and status[1] == -4 and steps[0] == 300
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_batch_auto_own_kernels_bitwise(L, geom, rule):
+    """The automatic schedule: lattices of over 10^5 units (64^3 BCC cells)
+    run each chunk with their own graph-replayed kernels, the small ones in
+    the persistent launch of the same chunk; every member equals its lone
+    run bitwise."""
+    m = geom.sphere_array(64, "bcc", c=0.3)
+    lats = [dict(mask=m, set_=st, tau=t, Lambda=lam, force=(1e-5, 0, 0))
+            for st, t, lam in (("B", 0.8, 3 / 16), ("D", 1.3, 3 / 16), ("C", 0.9, 3 / 16))]
+    lats += _lattices(geom)[:3]
+    B = L.LBMBatch(lats, precision="fp32", layout="sparse", check_interval=20, max_steps=1200,
+                   stop_rule=rule)
+    steps, status = B.run(1e-8)
+    sw, pe = B.schedule_counts()
+    assert sw > 0 and pe > 0, (sw, pe)
+    kb = B.permeability()
+    for i, l in enumerate(lats):
+        S = L.LBMSolver(l["mask"], l["set_"], l["tau"], l.get("Lambda", 3 / 16), l["force"],
+                        precision="fp32", layout="sparse", check_interval=20, max_steps=1200,
+                        stop_rule=rule)
+        rc, st = S.run_to_convergence(1e-8)
+        assert rc == status[i] and st == steps[i]
+        assert np.array_equal(S.get_populations(), B.lattice(i).get_populations())
+        assert np.array_equal(S.converged_permeability(), kb[i], equal_nan=True)
+        S.close()
