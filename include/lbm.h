@@ -167,6 +167,21 @@ int lbm_step(lbm_ctx *ctx, int64_t n);
  * way the results and the kernel-launch count are those of direct launches. */
 int lbm_run_to_convergence(lbm_ctx *ctx, double tol, int64_t *steps_taken);
 
+/* One evaluation of the stopping rule: the step count after the chunk, the
+ * measured mean velocity along the drive (U_b; under stop_rule 1 the mean of
+ * the chunk's last two steps) and the relative change |U_b - U_a| / |U_b|
+ * the rule compares with tol (NaN where no earlier value exists). */
+typedef struct {
+    int64_t step;
+    double U;
+    double change;
+} lbm_check;
+
+/* The checks of the last lbm_run_to_convergence, in order: copies up to cap
+ * records to out (nullable) and the total number to *count.  The record of a
+ * run: how the convergence measure of eq. (convergence) evolved. */
+int lbm_convergence_history(lbm_ctx *ctx, lbm_check *out, int64_t cap, int64_t *count);
+
 /* Mean velocity U[3] of the current state after streaming (not advanced). */
 int lbm_mean_velocity(lbm_ctx *ctx, double U[3]);
 
@@ -374,7 +389,9 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status);
 int lbm_batch_permeability(lbm_batch *b, double *k);
 int lbm_batch_mean_velocity(lbm_batch *b, double *U);
 /* Layout and nodes per thread chosen for each lattice (nullable outputs);
- * nodes_per_thread 0 marks a lattice that runs alone (see solo). */
+ * nodes_per_thread 0 marks a lattice that runs alone (see solo) or, under the
+ * automatic and grouped stepwise schedules, one of at least 1e5 units that
+ * runs its chunks on its own single-lattice kernels. */
 int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *nodes_per_thread);
 /* The context of lattice i (owned by the batch; valid until lbm_batch_destroy),
  * for the single-lattice readers (populations, velocity, checkpoint). */

@@ -707,6 +707,7 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
         // replayed; K even needs one graph, K odd two.
         AdjGraph graphs[2];
         bool unstable = false;
+        NvtxRange range("lbm_adjoint iterations");
         while (e == cudaSuccess && *iters < max_iter) {
             if (K >= 2 && *iters % K == 0 && max_iter - *iters >= K) {
                 AdjGraph *G = nullptr;
@@ -822,6 +823,7 @@ static int adjoint_run(lbm_ctx *c, double tol, int64_t max_iter, int d, double c
 // h_{n+1}; the context ends n steps on, at the forward sweep's final state.
 template <typename T>
 static int transient_run(lbm_ctx *c, int64_t n, int d, double coef, double sums[10]) {
+    NvtxRange range("lbm_adjoint_transient");
     const AdjView v = make_adj_view(c);
     const unsigned grid = (unsigned)((v.units + 255) / 256);
     for (int a = 0; a < 10; ++a) sums[a] = 0.0;

@@ -370,6 +370,7 @@ constexpr int64_t kMaxGraphChunk = 4096;
 // Falls back to direct launches where the stream cannot be captured (it is
 // being captured by the caller, or is the legacy default stream).
 static int enqueue_chunk(lbm_ctx *c, int64_t plain, int first, int nmeas) {
+    NvtxRange range("lbm chunk");
     const int phase = c->opt.layout == LBM_LAYOUT_AB ? c->cur : (int)(c->steps & 1);
     if (plain + nmeas < 2 || plain > kMaxGraphChunk) {
         enqueue_chunk_direct(c, plain, first, nmeas);
@@ -444,6 +445,15 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
     double Ua = NAN, Ub = NAN;
     double Uc3[3] = {NAN, NAN, NAN};
     int rc = LBM_ENOTCONV;
+    c->history.clear();
+    NvtxRange range("lbm_run_to_convergence");
+    auto note = [&]() {
+        lbm_check r;
+        r.step = c->steps;
+        r.U = Ub;
+        r.change = isfinite(Ua) ? fabs(Ub - Ua) / fabs(Ub) : NAN;
+        c->history.push_back(r);
+    };
     while (done < maxs) {
         int64_t chunk = K < maxs - done ? K : maxs - done;
         int rr;
@@ -464,6 +474,7 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
             Ua = 0.5 * (c->h_U[d] + c->h_U[3 + d]);
             Ub = Uc3[d];
             done += chunk;
+            note();
             const int flag = *(int *)(c->h_U + 24);
             if (flag || !isfinite(c->h_U[6]) || !isfinite(c->h_U[7]) || !isfinite(c->h_U[8])) {
                 rc = LBM_EUNSTABLE;
@@ -492,6 +503,7 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
             Ub = c->h_U[3 + d];
         }
         done += chunk;
+        note();
         const int flag = *(int *)(c->h_U + 24);
         if (flag || !isfinite(c->h_U[3]) || !isfinite(c->h_U[4]) || !isfinite(c->h_U[5])) {
             rc = LBM_EUNSTABLE;
@@ -510,6 +522,15 @@ int lbm_run_to_convergence(lbm_ctx *c, double tol, int64_t *steps_taken) {
         for (int a = 0; a < 3; ++a) c->U_conv[a] = Uc3[a];
     }
     return rc;
+}
+
+int lbm_convergence_history(lbm_ctx *c, lbm_check *out, int64_t cap, int64_t *count) {
+    if (!c || cap < 0) return LBM_EINVAL;
+    const int64_t n = (int64_t)c->history.size();
+    if (out)
+        for (int64_t i = 0; i < n && i < cap; ++i) out[i] = c->history[(size_t)i];
+    if (count) *count = n;
+    return LBM_OK;
 }
 
 int lbm_device_flags(lbm_ctx *c, int32_t *flags) {

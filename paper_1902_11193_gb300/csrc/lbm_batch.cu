@@ -1112,7 +1112,9 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
     const int64_t K = b->opt.check_interval;
     bool dirty = true, dirty_step = true;
     int nact = b->n - nsolo;
+    NvtxRange range("lbm_batch_run");
     while (nact > 0) {
+        NvtxRange chunk_range("lbm batch chunk");
         cudaError_t e;
         // schedule 2: grouped multi-lattice launches per step.  Otherwise,
         // under the automatic schedule, lattices that fill the GPU alone run
@@ -1283,9 +1285,15 @@ int lbm_batch_mean_velocity(lbm_batch *b, double *U) {
 
 int lbm_batch_config(lbm_batch *b, int32_t *layout, int32_t *npt) {
     if (!b) return LBM_EINVAL;
+    const bool own = b->opt.schedule == 0 || (b->opt.schedule == 2 && b->d_step_tiles);
     for (int i = 0; i < b->n; ++i) {
         if (layout) layout[i] = b->layout[i];
-        if (npt) npt[i] = b->npt[i];
+        if (npt) {
+            // a lattice that runs its chunks on its own kernels is in no tile
+            const lbm_ctx *c = b->ctx[i];
+            const int64_t units = b->layout[i] == LBM_LAYOUT_SPARSE ? c->Nf : c->N;
+            npt[i] = own && units >= kDirectUnits ? 0 : b->npt[i];
+        }
     }
     return LBM_OK;
 }

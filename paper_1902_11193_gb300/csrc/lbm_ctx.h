@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lbm.h"
 
 namespace lbm {
@@ -66,4 +68,5 @@ struct lbm_ctx {
     double U_conv[3];     // the mean velocity that run stopped on
     lbm::ChunkGraph graphs[lbm::kChunkGraphs];  // exec == nullptr: unused
     int next_graph;       // round-robin slot for the next capture
+    std::vector<lbm_check> history;  // the checks of the last lbm_run_to_convergence
 };

@@ -5,6 +5,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "lbm.h"
@@ -243,6 +244,15 @@ struct Reduce {
 };
 
 int launch_error(cudaError_t e);
+
+// A named NVTX range over a host scope (convergence chunks, batch chunks,
+// adjoint iterations), visible in profilers' timelines; no cost without one.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace lbm
 

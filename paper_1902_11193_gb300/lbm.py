@@ -11,7 +11,10 @@ CUDA device is present the calls raise.
 from __future__ import annotations
 
 import ctypes as C
+import json
+import math
 import os
+import time
 
 import numpy as np
 
@@ -42,6 +45,10 @@ class Grad(C.Structure):
                 ("dk_dLambda_q", C.c_double), ("dk_dLambda_m", C.c_double),
                 ("dk_dF", C.c_double * 3), ("dk_ds", C.c_double * 6), ("k", C.c_double),
                 ("iterations", C.c_int64), ("residual", C.c_double)]
+
+
+class Check(C.Structure):
+    _fields_ = [("step", C.c_int64), ("U", C.c_double), ("change", C.c_double)]
 
 
 class LatticeDesc(C.Structure):
@@ -109,6 +116,8 @@ def lib():
             "lbm_mean_velocity_noalloc": (C.c_int, [vp, vp, i32p, dp, vp, vp]),
             "lbm_converged_velocity": (C.c_int, [vp, dp]),
             "lbm_device_flags": (C.c_int, [vp, C.POINTER(i32)]),
+            "lbm_convergence_history": (C.c_int, [vp, C.POINTER(Check), i64,
+                                                  C.POINTER(i64)]),
             "lbm_converged_permeability": (C.c_int, [vp, dp]),
             "lbm_batch_default_options": (None, [C.POINTER(BatchOptions)]),
             "lbm_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(LatticeDesc),
@@ -130,6 +139,11 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def _json_float(v):
+    v = float(v)
+    return v if math.isfinite(v) else None
 
 
 def _check(rc: int, what: str) -> None:
@@ -255,10 +269,59 @@ class LBMSolver:
     def run_to_convergence(self, tol: float, raise_on_failure: bool = True):
         """Returns (status code, steps taken by this call)."""
         steps = C.c_int64(0)
+        t0 = time.perf_counter()
         rc = lib().lbm_run_to_convergence(self._h, float(tol), C.byref(steps))
+        self._last_run = dict(status=ERRORS.get(rc, rc), tol=float(tol), steps=int(steps.value),
+                              wall_s=time.perf_counter() - t0)
         if rc not in (0, -4) and raise_on_failure:
             raise LBMError(rc, "lbm_run_to_convergence")
         return rc, int(steps.value)
+
+    def convergence_history(self) -> np.ndarray:
+        """The checks of the last run_to_convergence (lbm_convergence_history):
+        a structured array of (step, U along the drive, relative change)."""
+        n = C.c_int64(0)
+        _check(lib().lbm_convergence_history(self._h, None, 0, C.byref(n)),
+               "lbm_convergence_history")
+        buf = (Check * max(n.value, 1))()
+        _check(lib().lbm_convergence_history(self._h, buf, n.value, C.byref(n)),
+               "lbm_convergence_history")
+        out = np.zeros(n.value, dtype=[("step", np.int64), ("U", np.float64),
+                                       ("change", np.float64)])
+        for i in range(n.value):
+            out[i] = (buf[i].step, buf[i].U, buf[i].change)
+        return out
+
+    def run_record(self) -> dict:
+        """A JSON-serialisable record of the last run_to_convergence: the
+        configuration, the status, steps and wall time, every check of the
+        stopping rule and the converged velocity and permeability."""
+        o = self.options if hasattr(self, "options") else None
+        last = getattr(self, "_last_run", None)
+        rec = {
+            "dims": [int(v) for v in self.dims],
+            "tau": float(self.tau),
+            "force": [float(v) for v in self.force],
+            "precision": {v: k for k, v in PRECISIONS.items()}.get(o.precision) if o else None,
+            "layout": {v: k for k, v in LAYOUTS.items()}.get(o.layout) if o else None,
+            "stop_rule": int(o.stop_rule) if o else None,
+            "check_interval": int(o.check_interval) if o else None,
+            "run": last,
+            "steps_total": self.steps,
+            "kernel_launches": self.kernel_launches,
+        }
+        h = self.convergence_history()
+        rec["history"] = [{"step": int(r["step"]), "U": _json_float(r["U"]),
+                           "change": _json_float(r["change"])} for r in h]
+        if last is not None and last["status"] in ("OK", "ENOTCONV") and len(h):
+            rec["U_conv"] = [float(v) for v in self.converged_velocity()]
+            rec["k_conv"] = [float(v) for v in self.converged_permeability()]
+        return rec
+
+    def write_run_record(self, path: str) -> None:
+        with open(path, "w") as fh:
+            json.dump(self.run_record(), fh, indent=1)
+            fh.write("\n")
 
     # -------------------------------------------------------------- outputs
     def mean_velocity(self) -> np.ndarray:

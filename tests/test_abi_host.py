@@ -73,6 +73,19 @@ def test_create_rejects_bad_arguments(L):
         L.LBMSolver(m, rates_=s)
 
 
+def test_null_handles_are_rejected(L):
+    """Calls that need no device reject a null context before touching it."""
+    import ctypes as C
+
+    lib = L.lib()
+    n = C.c_int64(7)
+    assert lib.lbm_convergence_history(None, None, 0, C.byref(n)) == -1 and n.value == 7
+    f = C.c_int32(0)
+    assert lib.lbm_device_flags(None, C.byref(f)) == -1
+    sw, pe = C.c_int64(0), C.c_int64(0)
+    assert lib.lbm_batch_schedule_counts(None, C.byref(sw), C.byref(pe)) == -1
+
+
 def test_strerror_covers_codes(L):
     lib = L.lib()
     for code in range(0, -9, -1):

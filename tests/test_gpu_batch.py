@@ -67,12 +67,17 @@ def test_batch_bitwise_equals_single_runs(L, geom, precision, layout, npt, rule,
         assert np.array_equal(S.converged_permeability(), kb[i], equal_nan=True)
 
 
+@pytest.mark.parametrize("npt", [1, 2])
 @pytest.mark.parametrize("rule", [0, 1])
-def test_batch_fp64_matches_oracle(L, ora, geom, rule):
+def test_batch_fp64_matches_oracle(L, ora, geom, rule, npt):
+    """Both tile shapes of the persistent kernel (one and two fluid nodes per
+    thread) against the oracle's converged permeability."""
     lats = _lattices(geom)[:3]
-    B = L.LBMBatch(lats, precision="fp64", layout="sparse", check_interval=10, stop_rule=rule)
+    B = L.LBMBatch(lats, precision="fp64", layout="sparse", nodes_per_thread=npt,
+                   check_interval=10, stop_rule=rule, schedule="persistent")
     steps, status = B.run(1e-9)
     assert np.all(status == 0)
+    assert np.all(B.config()[1] == npt)
     kb = B.permeability()
     for i, l in enumerate(lats):
         O = ora.Solver(l["mask"], ora.rates(l["set_"], l["tau"], l.get("Lambda", 3 / 16)),
@@ -186,6 +191,8 @@ def test_batch_auto_own_kernels_bitwise(L, geom, rule):
     steps, status = B.run(1e-8)
     sw, pe = B.schedule_counts()
     assert sw > 0 and pe > 0, (sw, pe)
+    nps = B.config()[1]
+    assert np.all(nps[:3] == 0) and np.all(nps[3:] > 0)  # own kernels vs tiles
     kb = B.permeability()
     for i, l in enumerate(lats):
         S = L.LBMSolver(l["mask"], l["set_"], l["tau"], l.get("Lambda", 3 / 16), l["force"],
