@@ -28,6 +28,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <new>
 #include <string>
@@ -438,6 +439,10 @@ struct lbm_batch {
     char *d_want;
     int64_t stepwise_chunks, persistent_chunks;
     std::vector<uint32_t> goff;
+    // automatic schedule: side streams for lattices stepped concurrently
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork;
 };
 
 extern "C" {
@@ -460,7 +465,11 @@ void lbm_batch_default_options(lbm_batch_options *o) {
 
 void lbm_batch_destroy(lbm_batch *b) {
     if (!b) return;
+    for (cudaStream_t st : b->side) cudaStreamSynchronize(st);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->side_done) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     for (lbm_ctx *c : b->ctx) lbm_destroy(c);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     cudaFree(b->d_lats);
@@ -577,6 +586,97 @@ size_t lat_bytes(const lbm_batch *b, const BatchLat &L) {
 #define LBM_STEP_DIRECT_UNITS 100000
 #endif
 constexpr int64_t kDirectUnits = LBM_STEP_DIRECT_UNITS;
+
+// Under the automatic schedule, up to LBM_BATCH_STREAMS such lattices run
+// their chunks at the same time, each on a side stream, as long as their
+// states together fit LBM_BATCH_CONC_L2_PERCENT of the L2 cache.  A lone
+// single-lattice launch leaves most SMs idle in its last wave, and between
+// its kernels; concurrent lattices fill those gaps.  Groups run in turn,
+// forked from and joined back into the batch's stream.
+#ifndef LBM_BATCH_STREAMS
+#define LBM_BATCH_STREAMS 4
+#endif
+#ifndef LBM_BATCH_CONC_L2_PERCENT
+#define LBM_BATCH_CONC_L2_PERCENT 60
+#endif
+
+// Creates the side streams and events once; returns how many are usable
+// (0: every lattice runs on the batch's stream).
+static int side_streams(lbm_batch *b) {
+    if (!b->side.empty() || LBM_BATCH_STREAMS < 2) return (int)b->side.size();
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        b->fork = nullptr;
+        return 0;
+    }
+    for (int j = 0; j < LBM_BATCH_STREAMS; ++j) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(st);
+            break;
+        }
+        b->side.push_back(st);
+        b->side_done.push_back(ev);
+    }
+    cudaGetLastError();
+    return (int)b->side.size();
+}
+
+// Enqueues one chunk (plain steps, then nmeas measuring steps) of each
+// lattice in `ids` with its own kernels: in groups of up to
+// LBM_BATCH_STREAMS lattices on the side streams, each group joined into
+// the batch's stream before the next one forks.  Groups are packed first
+// fit, largest state first, so that a large lattice shares its group with
+// small ones where the budget allows.  The lattices' results are bitwise
+// those of a sequential run: no lattice reads another's data.
+static int run_direct(lbm_batch *b, const std::vector<int> &ids, const std::vector<BatchLat> &lats,
+                      int64_t plain, int nmeas) {
+    const int ns = side_streams(b);
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t budget = (size_t)(l2 > 0 ? l2 : (64 << 20)) * LBM_BATCH_CONC_L2_PERCENT / 100;
+    std::vector<int> order(ids);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return lat_bytes(b, lats[x]) > lat_bytes(b, lats[y]);
+    });
+    std::vector<std::vector<int>> groups;
+    std::vector<size_t> used;
+    for (const int i : order) {
+        const size_t by = lat_bytes(b, lats[i]);
+        size_t g = 0;
+        while (g < groups.size() && !((int)groups[g].size() < ns && used[g] + by <= budget)) ++g;
+        if (g == groups.size()) {
+            groups.emplace_back();
+            used.push_back(0);
+        }
+        groups[g].push_back(i);
+        used[g] += by;
+    }
+    for (const std::vector<int> &grp : groups) {
+        const bool fork = grp.size() > 1;
+        if (fork && cudaEventRecord(b->fork, b->stream) != cudaSuccess) return LBM_ECUDA;
+        for (size_t m = 0; m < grp.size(); ++m) {
+            lbm_ctx *c = b->ctx[grp[m]];
+            const cudaStream_t own = c->stream;
+            const int j = (int)m;
+            if (fork) {
+                if (cudaStreamWaitEvent(b->side[j], b->fork, 0) != cudaSuccess) return LBM_ECUDA;
+                c->stream = b->side[j];
+            }
+            const int64_t l0 = c->launches;
+            const int rc = enqueue_measured_chunk(c, plain, nmeas);
+            c->stream = own;
+            b->launches += c->launches - l0;
+            if (rc != LBM_OK) return rc;
+            if (fork && (cudaEventRecord(b->side_done[j], b->side[j]) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->stream, b->side_done[j], 0) != cudaSuccess))
+                return LBM_ECUDA;
+        }
+    }
+    return LBM_OK;
+}
 
 // Share of the L2 cache a group of lattices may fill (percent).
 #ifndef LBM_STEP_L2_PERCENT
@@ -1137,15 +1237,11 @@ int lbm_batch_run(lbm_batch *b, double tol, int64_t *steps, int32_t *status) {
             if (e != cudaSuccess) return launch_error(e);
             b->stepwise_chunks++;
         } else {
-            for (const int i : direct_now) {
-                lbm_ctx *c = b->ctx[i];
-                const int64_t l0 = c->launches;
-                if (enqueue_measured_chunk(c, K - (b->opt.stop_rule == 1 ? 3 : 2),
-                                           b->opt.stop_rule == 1 ? 3 : 2) != LBM_OK)
-                    return LBM_ECUDA;
-                b->launches += c->launches - l0;
+            if (!direct_now.empty()) {
+                const int nm = b->opt.stop_rule == 1 ? 3 : 2;
+                if (run_direct(b, direct_now, lats, K - nm, nm) != LBM_OK) return LBM_ECUDA;
+                b->stepwise_chunks++;
             }
-            if (!direct_now.empty()) b->stepwise_chunks++;
             if ((int)direct_now.size() < nact) {
                 if (dirty) {
                     b->in_direct.assign(b->n, 0);

@@ -69,4 +69,5 @@ struct lbm_ctx {
     lbm::ChunkGraph graphs[lbm::kChunkGraphs];  // exec == nullptr: unused
     int next_graph;       // round-robin slot for the next capture
     std::vector<lbm_check> history;  // the checks of the last lbm_run_to_convergence
+    int odd_npt;          // sparse odd step: fluid nodes per thread (0: not chosen yet)
 };

@@ -629,6 +629,45 @@ SparseMap sparse_map(const lbm_ctx *c) {
     return m;
 }
 
+// Fluid nodes per thread of the odd step's lean kernel for this lattice:
+// four (the next record loaded ahead, fewest blocks) unless fewer leave less
+// of the last wave idle.  The work a launch is charged is its number of
+// waves (blocks over resident blocks of the GPU) times the nodes per thread;
+// ties go to more nodes per thread.  At 96^3 (about 600k fluid nodes) four
+// per thread fill 1.3 waves and two per thread 2.6.
+template <typename S, int K>
+static int odd_nodes_per_thread(lbm_ctx *c) {
+    if (c->odd_npt) return c->odd_npt;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_l<S, 4, K, false>, 256, 0);
+    cudaGetLastError();
+    const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : LBM_SPARSE_MIN_BLOCKS);
+    int best = 4;
+    int64_t best_work = INT64_MAX;
+    for (const int n : {4, 2, 1}) {
+        const int64_t blocks = (c->Nf + 256 * n - 1) / (256 * n);
+        const int64_t work = (blocks + slots - 1) / slots * n;
+        if (work < best_work) {
+            best_work = work;
+            best = n;
+        }
+    }
+    c->odd_npt = best;
+    return best;
+}
+
+template <typename S, int NPT, int K>
+static void launch_odd_lean(lbm_ctx *c, bool reduce, const OddMap &o, S *A, uint32_t Nf,
+                            const Collide<typename Store<S>::C> &p, float lds, float sts,
+                            const Reduce &red) {
+    const unsigned tg = (unsigned)((Nf + 256u * NPT - 1) / (256u * NPT));
+    if (reduce)
+        k_sparse_odd_l<S, NPT, K, true><<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
+    else
+        k_sparse_odd_l<S, NPT, K, false><<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
+}
+
 template <typename S, int K>
 int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &p) {
     const int bs = c->opt.block_size;
@@ -693,12 +732,11 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
             if constexpr (sizeof(S) <= 4 && LBM_ODD_LEAN) {
                 if (narrow_index(c) && c->d_orec) {
                     const OddMap o = odd_map(c);
-                    if (reduce)
-                        k_sparse_odd_l<S, LBM_SPARSE_ODD_NPT, K, true>
-                            <<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
-                    else
-                        k_sparse_odd_l<S, LBM_SPARSE_ODD_NPT, K, false>
-                            <<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
+                    switch (odd_nodes_per_thread<S, K>(c)) {
+                    case 1: launch_odd_lean<S, 1, K>(c, reduce, o, A, Nf, p, lds, sts, red); break;
+                    case 2: launch_odd_lean<S, 2, K>(c, reduce, o, A, Nf, p, lds, sts, red); break;
+                    default: launch_odd_lean<S, 4, K>(c, reduce, o, A, Nf, p, lds, sts, red); break;
+                    }
                     lean = true;
                 }
             }
