@@ -271,20 +271,39 @@ __global__ void __launch_bounds__(256) k_adj_capture(const S *A, AdjView v, AdjS
 // that each kernel carries only its own index arithmetic.  Sparse nodes use
 // the interior upstream formulas and redo the x-moving directions with the
 // periodic wrap only on the x faces (as the forward odd step does).
-// One unit per thread, four blocks per SM (FP32: 64 registers).  Tiles of
-// two or four units per thread, as the forward odd step uses, ran 3.5x
-// slower here.
-// CHK: a checking launch (residual partials); its own instantiation, so
-// that the plain launches carry none of its registers.
+// One unit per thread, four blocks per SM (FP32: 64 registers).  The plain
+// launches of the lean index path take LBM_ADJ_LEAN_NPT units per thread,
+// 256 apart, and load the next unit's record while the current one gathers
+// (64 registers, four blocks per SM).  At 256^3: one unit per thread at five
+// blocks per SM (48 registers, an 8-byte spill) 32.4-32.6k fluid MLUPS over
+// whole adjoint runs; two units per thread 33.0k; four (56 B of spills)
+// 28.9k; one unit at four or six blocks per SM 31.6k and 30.1k.
+// CHK: a checking launch (residual partials, one per block of 256 units);
+// its own instantiation, so that the plain launches carry none of its
+// registers, and always one unit per thread.  On the lean path it runs at
+// three blocks per SM (80 registers) rather than two (114): whole runs
+// 33.1k -> 33.2k fluid MLUPS at 256^3.
 #ifndef LBM_ADJ_LEAN_MIN_BLOCKS
-#define LBM_ADJ_LEAN_MIN_BLOCKS 5  // 48 registers (8-B spill): 3% faster than four
+#define LBM_ADJ_LEAN_MIN_BLOCKS 4
+#endif
+#ifndef LBM_ADJ_LEAN_NPT
+#define LBM_ADJ_LEAN_NPT 2
 #endif
 template <typename T, bool FROM_H, bool SP, bool CHK, bool LEAN = false>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : (LEAN ? LBM_ADJ_LEAN_MIN_BLOCKS : 4))
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2
+                                       : (LEAN ? (CHK ? 3 : LBM_ADJ_LEAN_MIN_BLOCKS) : (CHK ? 2 : 4)))
     k_adj_step(const T *__restrict__ H, const T *__restrict__ psi_in, T *__restrict__ psi_out,
                AdjView v, Collide<T> p, T coef, int d, double *partials) {
-    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NT = (SP && LEAN && !CHK) ? LBM_ADJ_LEAN_NPT : 1;
+    const uint32_t u0 = blockIdx.x * 256u * NT + threadIdx.x;
     T r[2] = {T(0), T(0)};  // residual terms of this node, in the iteration's precision
+    uint2 nrec = make_uint2(0u, 0u);  // lean path: the record of the next unit
+    if (SP && LEAN && u0 < v.units) nrec = __ldg(v.om.rec + u0);
+#pragma unroll 1
+    for (int t = 0; t < NT; ++t) {
+    const uint32_t u = u0 + 256u * t;
+    const uint2 rec = nrec;
+    if (SP && LEAN && t + 1 < NT && u + 256u < v.units) nrec = __ldg(v.om.rec + u + 256u);
     if (u < v.units) {
         T phi[Q];
         bool fluid = true;
@@ -296,7 +315,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : (LEAN ? LBM_A
             // solid: exactly where psi_i(x + c_i) (or the bounceback value)
             // sits in the two-array layout
             uint32_t loc[Q];
-            odd_lean_locations(v.om, u, __ldg(v.om.rec + u), loc);
+            odd_lean_locations(v.om, u, rec, loc);
             phi[0] = psi_in[u];
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
@@ -400,6 +419,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 || CHK ? 2 : (LEAN ? LBM_A
             for (int i = 0; i < Q; ++i) psi_out[(size_t)i * v.units + u] = T(0);
         }
     }
+    }
     if (CHK) block_sum2<T>(r[0], r[1], partials);
 }
 
@@ -425,8 +445,9 @@ void launch_adj_step(lbm_ctx *c, const AdjView &v, const T *H, const T *psi_in, 
             k_adj_step<T, FROM_H, true, true, true><<<grid, 256, 0, c->stream>>>(
                 H, psi_in, psi_out, v, p, coef, d, partials);
         else
-            k_adj_step<T, FROM_H, true, false, true><<<grid, 256, 0, c->stream>>>(
-                H, psi_in, psi_out, v, p, coef, d, nullptr);
+            k_adj_step<T, FROM_H, true, false, true>
+                <<<(v.units + 256u * LBM_ADJ_LEAN_NPT - 1) / (256u * LBM_ADJ_LEAN_NPT), 256, 0,
+                   c->stream>>>(H, psi_in, psi_out, v, p, coef, d, nullptr);
         c->launches++;
         return;
     }
