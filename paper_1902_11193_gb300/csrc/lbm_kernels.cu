@@ -630,11 +630,11 @@ SparseMap sparse_map(const lbm_ctx *c) {
 }
 
 // Fluid nodes per thread of the odd step's lean kernel for this lattice:
-// four (the next record loaded ahead, fewest blocks) unless fewer leave less
-// of the last wave idle.  The work a launch is charged is its number of
-// waves (blocks over resident blocks of the GPU) times the nodes per thread;
-// ties go to more nodes per thread.  At 96^3 (about 600k fluid nodes) four
-// per thread fill 1.3 waves and two per thread 2.6.
+// four (the next record loaded ahead, fewest blocks) while the grid still
+// gives every SM its resident blocks, else two, else one, so that a small
+// lattice keeps all SMs busy.  FP32 per launch: 64^3 Boolean (104k fluid
+// nodes) 12.3 us with four per thread, 9.3 us with one; from 128^3 up four
+// are best (256^3: 223, 228 and 241 us with four, two and one).
 template <typename S, int K>
 static int odd_nodes_per_thread(lbm_ctx *c) {
     if (c->odd_npt) return c->odd_npt;
@@ -643,14 +643,11 @@ static int odd_nodes_per_thread(lbm_ctx *c) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_l<S, 4, K, false>, 256, 0);
     cudaGetLastError();
     const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : LBM_SPARSE_MIN_BLOCKS);
-    int best = 4;
-    int64_t best_work = INT64_MAX;
-    for (const int n : {4, 2, 1}) {
-        const int64_t blocks = (c->Nf + 256 * n - 1) / (256 * n);
-        const int64_t work = (blocks + slots - 1) / slots * n;
-        if (work < best_work) {
-            best_work = work;
+    int best = 1;
+    for (const int n : {4, 2}) {
+        if ((c->Nf + 256 * n - 1) / (256 * n) >= slots) {
             best = n;
+            break;
         }
     }
     c->odd_npt = best;
