@@ -72,7 +72,8 @@ def build_lbm(force: bool = False, extra_flags: list[str] | None = None,
     with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = so + f".tmp{os.getpid()}"
-    subprocess.run([_nvcc(), "-shared", *NVCC_ARCH, "-o", tmp, *objs, "-lcudart"], check=True)
+    subprocess.run([_nvcc(), "-shared", *NVCC_ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"],
+                   check=True)
     os.replace(tmp, so)
     return so
 

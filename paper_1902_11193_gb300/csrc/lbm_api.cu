@@ -6,7 +6,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "lbm_internal.cuh"
@@ -51,6 +53,66 @@ using namespace lbm;
         cudaError_t e_ = (call);                  \
         if (e_ != cudaSuccess) return launch_error(e_); \
     } while (0)
+
+// Fluid count and value check of a host mask (every byte 0 or 1): eight
+// bytes at a time (the set bits of 0/1 bytes are the solid voxels; any byte
+// above 1 leaves a bit outside 0x01 in the OR of all words), split over up
+// to 16 host threads for masks of 8 Mi voxels and more.  A 512^3 mask took
+// 15 ms one byte at a time.
+static void scan_range(const uint8_t *mask, int64_t b, int64_t e, uint64_t *acc_out,
+                       int64_t *ones_out) {
+    uint64_t acc = 0;
+    int64_t ones = 0;
+    int64_t n = b;
+    for (; n + 8 <= e; n += 8) {
+        uint64_t w;
+        memcpy(&w, mask + n, 8);
+        acc |= w;
+        ones += __builtin_popcountll(w);
+    }
+    for (; n < e; ++n) {
+        acc |= mask[n];
+        ones += __builtin_popcountll(mask[n]);
+    }
+    *acc_out = acc;
+    *ones_out = ones;
+}
+
+static bool scan_mask(const uint8_t *mask, int64_t N, int64_t *Nf) {
+    constexpr int kMaxThreads = 16;
+    const unsigned hw = std::thread::hardware_concurrency();
+    int nt = (int)std::min<int64_t>(N >> 23, (int64_t)(hw > 0 ? hw : 1));
+    nt = std::max(1, std::min(nt, kMaxThreads));
+    uint64_t acc[kMaxThreads] = {};
+    int64_t ones[kMaxThreads] = {};
+    const int64_t per = ((N + nt - 1) / nt + 7) & ~int64_t(7);
+    std::vector<std::thread> pool;
+    int started = 1;
+    try {
+        for (int t = 1; t < nt; ++t) {
+            const int64_t b = std::min(N, t * per), e = std::min(N, b + per);
+            pool.emplace_back(scan_range, mask, b, e, &acc[t], &ones[t]);
+            ++started;
+        }
+    } catch (...) {  // no threads: the rest on this one
+    }
+    scan_range(mask, 0, std::min(N, per), &acc[0], &ones[0]);
+    for (std::thread &th : pool) th.join();
+    if (started < nt) {
+        const int64_t b = std::min(N, started * per);
+        scan_range(mask, b, N, &acc[started], &ones[started]);
+        started = std::min(started + 1, nt);
+    }
+    uint64_t all = 0;
+    int64_t solid = 0;
+    for (int t = 0; t < started; ++t) {
+        all |= acc[t];
+        solid += ones[t];
+    }
+    if (all & 0xFEFEFEFEFEFEFEFEull) return false;
+    *Nf = N - solid;
+    return true;
+}
 
 extern "C" {
 
@@ -183,21 +245,8 @@ int lbm_create_rates(lbm_ctx **out, const uint8_t *mask, const int32_t dims[3], 
                          !(o.rho_in > 0.0) || !(o.rho_out > 0.0) || !isfinite(o.rho_in) ||
                          !isfinite(o.rho_out)))
         return LBM_EINVAL;
-    // fluid count and value check in one branch-free pass (vectorised by the
-    // compiler; a 512^3 mask is 128 MiB of host memory)
     int64_t Nf = 0;
-    uint32_t bits = 0;
-    for (int64_t b = 0; b < N; b += 65536) {
-        const int64_t e = N - b < 65536 ? N : b + 65536;
-        uint32_t cnt = 0;
-        for (int64_t n = b; n < e; ++n) {
-            const uint32_t v = mask[n];
-            bits |= v;
-            cnt += v == 0u;
-        }
-        Nf += cnt;
-    }
-    if (bits > 1u) return LBM_EINVAL;
+    if (!scan_mask(mask, N, &Nf)) return LBM_EINVAL;
 
     lbm_ctx *c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ENOMEM;

@@ -61,6 +61,15 @@ def test_create_rejects_bad_arguments(L):
         with pytest.raises(L.LBMError) as e:
             L.LBMSolver(bad, "B", tau=1.0)
         assert e.value.code == -1
+    # masks of 2^24 voxels and more are scanned by several host threads:
+    # bad values at the start, across the split and at the end are caught
+    huge = np.zeros((256, 256, 256), np.uint8)
+    for flat in (0, huge.size // 2 - 1, huge.size // 2, huge.size - 1):
+        bad = huge.copy()
+        bad.reshape(-1)[flat] = 2
+        with pytest.raises(L.LBMError) as e:
+            L.LBMSolver(bad, "B", tau=1.0)
+        assert e.value.code == -1
     with pytest.raises(L.LBMError):
         L.LBMSolver(m, "B", tau=1.0, block_size=48)
     s = L.rates("B", 1.0)
