@@ -226,6 +226,31 @@ def test_wide_offsets_bitwise_equal(L, ora, geom, name, precision):
         assert dev_err(out[1][0], O.get_f()) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("edge", [96, 128])
+def test_odd_tile_widths_bitwise_equal(L, geom, edge, precision):
+    """The odd step's lean kernel takes four fluid nodes per thread while its
+    grid fills every SM, else two or one.  The Boolean 96^3 medium (about
+    352k fluid nodes) takes two, 128^3 (about 837k) four, the small lattices
+    above one.  Each is bitwise the general kernel of the 64-bit-offset path
+    over plain and measuring steps."""
+    mask = geom.boolean(edge, 10, 0.40, seed=1902_11193 + 1)[0]
+    f0 = random_state(mask, 1e-3, seed=23)
+    out = []
+    for width in (0, 64):
+        S = L.LBMSolver(mask, "B", 1.0, force=F3, layout="sparse", precision=precision,
+                        index_width=width, check_interval=6, max_steps=13)
+        S.set_populations(f0)
+        S.step(5)
+        f5 = S.get_populations()
+        rc, taken = S.run_to_convergence(0.0)
+        assert rc == -4 and taken == 13
+        out.append((f5, S.get_populations(), S.converged_velocity(), S.mean_velocity()))
+        S.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_config1_fp32_permeability(L, config1, layout):
     mask, steps, k_ora, _ = config1
