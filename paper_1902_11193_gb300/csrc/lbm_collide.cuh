@@ -175,8 +175,8 @@ __device__ __forceinline__ T half_of(int k, const Collide<T> &p) {
 template <typename T>
 __device__ __forceinline__ void eq_and_force(T rho, T jx, T jy, T jz, const Collide<T> &p,
                                              T meq[Q], T mF[Q]) {
-    const T q = p.linear ? T(0) : T(1);
-    const T q2 = p.linear ? T(0) : T(2);
+    const T q = p.q;
+    const T q2 = rmul(T(2), p.q);
     const T xx = rmul(jx, jx), yy = rmul(jy, jy), zz = rmul(jz, jz);
     const T jj = rmul(q, radd(radd(xx, yy), zz));
     const T qxx = rmul(q, rsub(rsub(rmul(T(2), xx), yy), zz));
@@ -296,7 +296,7 @@ __device__ __forceinline__ T pair_axis_sum(int a, const T d[9]) {
 template <typename T>
 __device__ __forceinline__ void trt_collide(T g[Q], const Collide<T> &p, T &jx_out, T &jy_out,
                                             T &jz_out) {
-    const T q = p.linear ? T(0) : T(1);
+    const T q = p.q;
     const T sp = p.snu, sm = p.sq, hp = p.hnu, hm = p.hq;  // s+, s-, 1 - s+/2, 1 - s-/2
     T sum[9], dif[9];
 #pragma unroll

@@ -52,6 +52,7 @@ struct Collide {
     T se, seps, sq, snu, spi, sm;  // diag(S) of eq. (MRT params), grouped
     T he, heps, hq, hnu, hpi, hm;  // 1 - s/2 of each group (forcing weight)
     T Fx, Fy, Fz;                  // body force density
+    T q;                           // weight of the quadratic equilibrium / forcing terms
     int linear;                    // drop quadratic equilibrium / forcing terms
     int trt;                       // one even and one odd rate: link-basis collision
 };
@@ -78,9 +79,27 @@ inline Collide<T> make_collide(const double s[19], const double F[3], int linear
     p.Fx = (T)F[0];
     p.Fy = (T)F[1];
     p.Fz = (T)F[2];
+    p.q = linear ? T(0) : T(1);
     p.linear = linear;
     // s_e = s_eps = s_nu = s_pi and s_q = s_m: the link-basis TRT form applies
     p.trt = allow_trt && s[1] == s[9] && s[2] == s[9] && s[10] == s[9] && s[16] == s[4];
+    return p;
+}
+
+// The collision of values scaled by sigma = 2^S: the FP16 storage kernels
+// that collide the stored halves as they are (h = 2^S (f - w)), without the
+// 2^-S multiply on load and the 2^S multiply on store.  The force is scaled
+// by sigma and the weight of the quadratic terms by 1/sigma.  Every
+// intermediate of the collision is then the unscaled one times an exact
+// power of two (both collision forms are sums and products of the values,
+// the force and constants, each product of two scaled factors met by q), so
+// the halves stored are bitwise those of the scaled loads and stores, and
+// the momentum is sigma times the unscaled one.
+inline Collide<float> scaled_collide(Collide<float> p, float sigma) {
+    p.Fx *= sigma;
+    p.Fy *= sigma;
+    p.Fz *= sigma;
+    p.q /= sigma;
     return p;
 }
 

@@ -177,6 +177,9 @@ __global__ void __launch_bounds__(256, LBM_SPARSE_MIN_BLOCKS)
     k_sparse_odd_l(S *A, OddMap o, uint32_t Nf, Collide<typename Store<S>::C> p, float ld_scale,
                    float st_scale, Reduce red) {
     using C = typename Store<S>::C;
+    // FP16 storage: p is scaled_collide's and the halves are collided as
+    // stored; ld_scale (2^-S) only unscales the measured momentum
+    constexpr bool kRaw = sizeof(S) == 2;
     __shared__ double wsum[RED ? NPT : 1][8][3];  // RED: warp sums of each group
     uint32_t k = blockIdx.x * (256u * NPT) + threadIdx.x;
     uint2 nxt = k < Nf ? __ldg(o.rec + k) : make_uint2(0u, 0u);
@@ -195,12 +198,28 @@ __global__ void __launch_bounds__(256, LBM_SPARSE_MIN_BLOCKS)
             odd_lean_locations(o, k, cur, loc);
             C g[Q];
 #pragma unroll
-            for (int j = 0; j < Q; ++j)
-                g[j] = in_range(loc[j], lim, o.flag) ? Store<S>::ld(A + loc[j], ld_scale) : C(0);
+            for (int j = 0; j < Q; ++j) {
+                if (!in_range(loc[j], lim, o.flag))
+                    g[j] = C(0);
+                else if constexpr (kRaw)
+                    g[j] = __half2float(A[loc[j]]);
+                else
+                    g[j] = Store<S>::ld(A + loc[j], ld_scale);
+            }
             collide_as<K, C>(g, p, jx, jy, jz);
 #pragma unroll
-            for (int j = 0; j < Q; ++j)
-                if (in_range(loc[j], lim, o.flag)) Store<S>::st(A + loc[j], g[opp(j)], st_scale);
+            for (int j = 0; j < Q; ++j) {
+                if (!in_range(loc[j], lim, o.flag)) continue;
+                if constexpr (kRaw)
+                    A[loc[j]] = __float2half_rn(g[opp(j)]);
+                else
+                    Store<S>::st(A + loc[j], g[opp(j)], st_scale);
+            }
+            if (kRaw) {  // the measured momentum in unscaled units
+                jx = __fmul_rn(jx, ld_scale);
+                jy = __fmul_rn(jy, ld_scale);
+                jz = __fmul_rn(jz, ld_scale);
+            }
         }
         if (RED) warp_momentum_store<C>(jx, jy, jz, valid, wsum[RED ? r : 0], red.flag);
         ++groups;
@@ -260,13 +279,17 @@ __global__ void __launch_bounds__(256, 2)
 // packed into one 32-bit register (half2), so the four nodes' loads fit the
 // registers the two-node FP32 kernel uses, and a warp keeps as many bytes
 // in flight as that kernel does (two-byte values need twice the loads).
+// p is scaled_collide's: the halves are collided as stored, and inv (2^-S)
+// only brings the measured momentum back to unscaled units.
 #ifndef LBM_EVEN_H4
 #define LBM_EVEN_H4 1  // 0: FP16 even steps through k_sparse_even_x2 as well
 #endif
+#ifndef LBM_EVEN_P2
+#define LBM_EVEN_P2 1  // 0: FP16 plain even steps through k_sparse_even_h4 also for even N_f
+#endif
 template <int K, bool RED>
 __global__ void __launch_bounds__(256, 2)
-    k_sparse_even_h4(__half *A, uint32_t Nf, Collide<float> p, float ld_scale, float st_scale,
-                     Reduce red) {
+    k_sparse_even_h4(__half *A, uint32_t Nf, Collide<float> p, float inv, Reduce red) {
     const uint32_t k0 = blockIdx.x * 1024u + threadIdx.x;
     __half2 h01[Q], h23[Q];  // (node 0, node 1) and (node 2, node 3) of this thread
     const __half z = __float2half_rn(0.f);
@@ -286,15 +309,17 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const __half2 h = r < 2 ? h01[j] : h23[j];
-            g[j] = __fmul_rn(__half2float((r & 1) ? __high2half(h) : __low2half(h)), ld_scale);
+            g[j] = __half2float((r & 1) ? __high2half(h) : __low2half(h));
         }
         float jx = 0.f, jy = 0.f, jz = 0.f;
         if (v) {
             collide_as<K, float>(g, p, jx, jy, jz);
 #pragma unroll
-            for (int j = 0; j < Q; ++j) Store<__half>::st(A + (uint32_t)j * Nf + k, g[opp(j)], st_scale);
+            for (int j = 0; j < Q; ++j) A[(uint32_t)j * Nf + k] = __float2half_rn(g[opp(j)]);
         }
-        if (RED) warp_momentum_store<float>(jx, jy, jz, v, wsum[RED ? r : 0], red.flag);
+        if (RED)
+            warp_momentum_store<float>(__fmul_rn(jx, inv), __fmul_rn(jy, inv), __fmul_rn(jz, inv), v,
+                                       wsum[RED ? r : 0], red.flag);
     }
     if (RED) {  // partials 4b .. 4b + 3 (nodes 256 g .. 256 g + 255, as in k_sparse)
         __syncthreads();
@@ -305,6 +330,43 @@ __global__ void __launch_bounds__(256, 2)
             const int r = threadIdx.x / 3, a = threadIdx.x % 3;
             red.partials[3 * (size_t)(g0 + (uint32_t)r) + a] = group_momentum_total(wsum[r], a);
         }
+    }
+}
+
+// Even steps, FP16 storage, N_f even (so every slot starts on a 4-byte
+// boundary), plain steps: the adjacent nodes 2m and 2m + 1 share one 32-bit
+// word per slot.  A thread loads and stores such a pair with one access per
+// slot and packs the pair's two results with one conversion, which takes
+// two of the six instructions per stored value of k_sparse_even_h4 away.
+// Two pairs per thread, 256 pairs apart (1024 nodes per block).  Measuring
+// steps keep k_sparse_even_h4, whose warps sum the nodes in the order of
+// every other kernel.  p is scaled_collide's (halves collided as stored).
+template <int K>
+__global__ void __launch_bounds__(256, 2)
+    k_sparse_even_p2(__half2 *A, uint32_t Nf, Collide<float> p) {
+    const uint32_t np = Nf / 2u;  // node pairs per slot
+    const uint32_t q0 = blockIdx.x * 512u + threadIdx.x, q1 = q0 + 256u;
+    const bool v0 = q0 < np, v1 = q1 < np;
+    const __half2 z = __float2half2_rn(0.f);
+    __half2 w0[Q], w1[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        w0[j] = v0 ? A[(uint32_t)j * np + q0] : z;
+        w1[j] = v1 ? A[(uint32_t)j * np + q1] : z;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (!(t ? v1 : v0)) continue;
+        const uint32_t q = t ? q1 : q0;
+        float ga[Q], gb[Q], jx, jy, jz;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) ga[j] = __low2float(t ? w1[j] : w0[j]);
+        collide_as<K, float>(ga, p, jx, jy, jz);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) gb[j] = __high2float(t ? w1[j] : w0[j]);
+        collide_as<K, float>(gb, p, jx, jy, jz);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) A[(uint32_t)j * np + q] = __floats2half2_rn(ga[opp(j)], gb[opp(j)]);
     }
 }
 
@@ -659,10 +721,12 @@ static void launch_odd_lean(lbm_ctx *c, bool reduce, const OddMap &o, S *A, uint
                             const Collide<typename Store<S>::C> &p, float lds, float sts,
                             const Reduce &red) {
     const unsigned tg = (unsigned)((Nf + 256u * NPT - 1) / (256u * NPT));
+    Collide<typename Store<S>::C> pk = p;
+    if constexpr (sizeof(S) == 2) pk = scaled_collide(p, sts);
     if (reduce)
-        k_sparse_odd_l<S, NPT, K, true><<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
+        k_sparse_odd_l<S, NPT, K, true><<<tg, 256, 0, c->stream>>>(A, o, Nf, pk, lds, sts, red);
     else
-        k_sparse_odd_l<S, NPT, K, false><<<tg, 256, 0, c->stream>>>(A, o, Nf, p, lds, sts, red);
+        k_sparse_odd_l<S, NPT, K, false><<<tg, 256, 0, c->stream>>>(A, o, Nf, pk, lds, sts, red);
 }
 
 template <typename S, int K>
@@ -696,12 +760,20 @@ int launch_step_k(lbm_ctx *c, bool reduce, const Collide<typename Store<S>::C> &
         if constexpr (sizeof(S) == 2 && LBM_EVEN_H4) {
             if (!odd && narrow_index(c)) {
                 const unsigned g4 = (unsigned)((c->Nf + 1023) / 1024);
+                const Collide<float> ps = scaled_collide(p, sts);
+                if (!reduce && LBM_EVEN_P2 && c->Nf % 2 == 0) {
+                    const unsigned gp = (unsigned)((c->Nf / 2 + 511) / 512);
+                    k_sparse_even_p2<K><<<gp, 256, 0, c->stream>>>((__half2 *)c->d_pop[0],
+                                                                   (uint32_t)c->Nf, ps);
+                    grid = gp;
+                    break;
+                }
                 if (reduce)
                     k_sparse_even_h4<K, true><<<g4, 256, 0, c->stream>>>(
-                        (__half *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                        (__half *)c->d_pop[0], (uint32_t)c->Nf, ps, lds, red);
                 else
                     k_sparse_even_h4<K, false><<<g4, 256, 0, c->stream>>>(
-                        (__half *)c->d_pop[0], (uint32_t)c->Nf, p, lds, sts, red);
+                        (__half *)c->d_pop[0], (uint32_t)c->Nf, ps, lds, red);
                 grid = reduce ? groups : g4;
                 break;
             }

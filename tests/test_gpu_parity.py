@@ -251,6 +251,39 @@ def test_odd_tile_widths_bitwise_equal(L, geom, edge, precision):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("st", ["B", "D"])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_fp16_scaled_kernels_bitwise_equal(L, geom, parity, st, linear):
+    """FP16 storage: the lean odd kernel and the even kernels collide the
+    stored halves as they are, with the force scaled by 2^S and the
+    quadratic terms by 2^-S, and plain even steps take adjacent node pairs
+    per 32-bit word when N_f is even.  Against the general kernels of the
+    64-bit-offset path, which multiply by 2^-S on load and 2^S on store:
+    bitwise the same populations and measured velocities, for N_f even and
+    odd, both collision forms (Set B: link-basis TRT; Set D: MRT) and the
+    linear equilibrium."""
+    mask = geom.boolean(48, 6, 0.35, seed=1902_11193 + 3)[0].copy()
+    fluid = np.flatnonzero(mask.reshape(-1) == 0)
+    if fluid.size % 2 != parity:  # one more solid voxel flips the parity
+        mask.reshape(-1)[fluid[fluid.size // 2]] = 1
+    assert int((mask == 0).sum()) % 2 == parity
+    f0 = random_state(mask, 1e-3, seed=29)
+    out = []
+    for width in (0, 64):
+        S = L.LBMSolver(mask, st, 0.9, force=F3, layout="sparse", precision="fp16",
+                        index_width=width, check_interval=6, max_steps=13, linear_eq=linear)
+        S.set_populations(f0)
+        S.step(5)
+        f5 = S.get_populations()
+        rc, taken = S.run_to_convergence(0.0)
+        assert rc == -4 and taken == 13
+        out.append((f5, S.get_populations(), S.converged_velocity(), S.mean_velocity()))
+        S.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_config1_fp32_permeability(L, config1, layout):
     mask, steps, k_ora, _ = config1
