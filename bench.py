@@ -366,7 +366,7 @@ def time_kernel_launches(S, n, stream, split=False):
 # kernels of each layout's plain stream-collide launches (even step, odd step)
 STEP_KERNELS = {
     ("sparse", "fp32"): ("k_sparse_even_x2", "k_sparse_odd_l"),
-    ("sparse", "fp16"): ("k_sparse_even_x2", "k_sparse_odd_l"),
+    ("sparse", "fp16"): ("k_sparse_even_h4", "k_sparse_odd_l"),
     ("sparse", "fp64"): ("k_sparse", "k_sparse_odd_t"),
     ("aa", "fp32"): ("k_aa<even>", "k_aa<odd>"), ("aa", "fp16"): ("k_aa<even>", "k_aa<odd>"),
     ("aa", "fp64"): ("k_aa<even>", "k_aa<odd>"),
@@ -418,6 +418,9 @@ def run_ours(args):
     achieved = bpu * nf / (kmean * 1e-3) / 1e9
     traffic = measured_traffic(args.layout, args.precision, nf)
     kern = STEP_KERNELS.get((args.layout, args.precision), ("k_ab", "k_ab"))
+    if (args.layout, args.precision) == ("sparse", "fp16"):
+        # plain FP16 even steps pair adjacent nodes per 32-bit word when N_f is even
+        kern = ("k_sparse_even_p2" if nf % 2 == 0 else "k_sparse_even_h4", kern[1])
 
     out = {
         "metric": "fluid MLUPS", "value": value, "unit": "fluid MLUPS", "n_gpus": ws,
