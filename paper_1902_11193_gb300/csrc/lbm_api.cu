@@ -87,6 +87,7 @@ static bool scan_mask(const uint8_t *mask, int64_t N, int64_t *Nf) {
     int64_t ones[kMaxThreads] = {};
     const int64_t per = ((N + nt - 1) / nt + 7) & ~int64_t(7);
     std::vector<std::thread> pool;
+    pool.reserve(nt);  // no reallocation while threads are being started
     int started = 1;
     try {
         for (int t = 1; t < nt; ++t) {

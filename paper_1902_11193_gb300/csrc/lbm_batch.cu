@@ -443,6 +443,7 @@ struct lbm_batch {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_done;
     cudaEvent_t fork;
+    bool side_tried;  // side streams created (or their creation failed) once
 };
 
 extern "C" {
@@ -602,24 +603,30 @@ constexpr int64_t kDirectUnits = LBM_STEP_DIRECT_UNITS;
 
 // Creates the side streams and events once; returns how many are usable
 // (0: every lattice runs on the batch's stream).
+// A failed creation is not retried; its error is cleared (and only then).
 static int side_streams(lbm_batch *b) {
-    if (!b->side.empty() || LBM_BATCH_STREAMS < 2) return (int)b->side.size();
+    if (b->side_tried || LBM_BATCH_STREAMS < 2) return (int)b->side.size();
+    b->side_tried = true;
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
         b->fork = nullptr;
+        cudaGetLastError();
         return 0;
     }
     for (int j = 0; j < LBM_BATCH_STREAMS; ++j) {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
             cudaStreamDestroy(st);
             break;
         }
         b->side.push_back(st);
         b->side_done.push_back(ev);
     }
-    cudaGetLastError();
     return (int)b->side.size();
 }
 

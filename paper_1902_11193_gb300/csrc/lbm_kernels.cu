@@ -701,9 +701,17 @@ template <typename S, int K>
 static int odd_nodes_per_thread(lbm_ctx *c) {
     if (c->odd_npt) return c->odd_npt;
     int sms = 0, per = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_l<S, 4, K, false>, 256, 0);
-    cudaGetLastError();
+    // a failed query falls back to defaults; its error is cleared, and only
+    // then, so that an earlier launch's error stays visible to the caller
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        sms = 0;
+        cudaGetLastError();
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sparse_odd_l<S, 4, K, false>, 256,
+                                                      0) != cudaSuccess) {
+        per = 0;
+        cudaGetLastError();
+    }
     const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : LBM_SPARSE_MIN_BLOCKS);
     int best = 1;
     for (const int n : {4, 2}) {
