@@ -390,16 +390,23 @@ def test_checkpoint_resume_bitwise(L, geom, tmp_path, layout, precision):
 
 # ------------------------------------------- full size, bench configuration
 
-@pytest.mark.parametrize("layout", ["aa", "sparse"])
-def test_512_boolean_sampled_parity(L, ora, geom, layout):
-    """512^3 Boolean medium (r = 10, porosity 0.40, Set B, tau = 1, F = 1e-6),
-    FP32 shifted, in the benchmark's launch configuration: after a few steps,
-    sampled nodes' next post-collision populations are recomputed by the
-    oracle from the GPU state of their upstream neighbourhood."""
+@pytest.mark.parametrize("layout,precision,warm,tol", [
+    ("aa", "fp32", 3, 1e-5), ("aa", "fp32", 2, 1e-5),
+    ("sparse", "fp32", 3, 1e-5), ("sparse", "fp32", 2, 1e-5),
+    ("sparse", "fp16", 3, 1e-3), ("sparse", "fp16", 2, 1e-3)])
+def test_512_boolean_sampled_parity(L, ora, geom, layout, precision, warm, tol):
+    """512^3 Boolean medium (r = 10, porosity 0.40, Set B, tau = 1, F = 1e-6)
+    in the benchmark's launch configuration: after `warm` steps, sampled
+    nodes' next post-collision populations are recomputed by the oracle from
+    the GPU state of their upstream neighbourhood.  warm = 3 checks an odd
+    step, 2 an even one.  FP32 storage within 1e-5 of the largest deviation
+    from rest; FP16 storage (the even step's node pairs, N_f being even
+    here, and the odd step's scaled collision) within 1e-3: the stored halves
+    round at 2^-11 of their values."""
     mask, _ = geom.boolean(512, 10, 0.40, seed=1902_11193 + 1)
     F = (1e-6, 0.0, 0.0)
-    S = L.LBMSolver(mask, "B", 1.0, force=F, layout=layout, precision="fp32")
-    S.step(3)
+    S = L.LBMSolver(mask, "B", 1.0, force=F, layout=layout, precision=precision)
+    S.step(warm)
     nodes = sample_nodes(mask, 400, seed=1)
     ups = upstream_nodes(mask, nodes)
     fstar = S.get_populations_at(ups.reshape(-1)).reshape(len(nodes), 19, 19)
@@ -414,7 +421,7 @@ def test_512_boolean_sampled_parity(L, ora, geom, layout):
         pred[k] = ora.collide(fl, s, F)
     S.step(1)
     got = S.get_populations_at(nodes)
-    assert dev_err(got.T, pred.T) <= 1e-5
+    assert dev_err(got.T, pred.T) <= tol
     nf, _ = S.link_counts()
     assert nf == int((mask == 0).sum())
 
