@@ -426,6 +426,35 @@ def test_512_boolean_sampled_parity(L, ora, geom, layout, precision, warm, tol):
     assert nf == int((mask == 0).sum())
 
 
+@pytest.mark.parametrize("precision,warm,tol", [
+    ("fp32", 3, 1e-5), ("fp16", 3, 1e-3), ("fp16", 2, 1e-3)])
+def test_1024_boolean_sampled_parity(L, ora, geom, precision, warm, tol):
+    """The large low-porosity image: 1024^3 Boolean medium (r = 8, porosity
+    0.20, Set D: the moment-space MRT collision, tau = 1, F = 1e-6), sparse,
+    as the bench's 1024^3 leg runs it (19 N_f just under 2^32: 32-bit
+    offsets).  Sampled nodes' next post-collision populations against the
+    oracle's collision of the GPU's upstream state, as at 512^3."""
+    mask, _ = geom.boolean(1024, 8, 0.20, seed=1902_11193 + 5)
+    F = (1e-6, 0.0, 0.0)
+    S = L.LBMSolver(mask, "D", 1.0, force=F, layout="sparse", precision=precision)
+    S.step(warm)
+    nodes = sample_nodes(mask, 300, seed=2)
+    ups = upstream_nodes(mask, nodes)
+    fstar = S.get_populations_at(ups.reshape(-1)).reshape(len(nodes), 19, 19)
+    s = ora.rates("D", 1.0)
+    pred = np.zeros((len(nodes), 19))
+    flat = mask.reshape(-1)
+    for k in range(len(nodes)):
+        fl = np.empty(19)
+        for i in range(19):
+            fl[i] = fstar[k, 0, OPP[i]] if flat[ups[k, i]] else fstar[k, i, i]
+        pred[k] = ora.collide(fl, s, F)
+    S.step(1)
+    got = S.get_populations_at(nodes)
+    assert dev_err(got.T, pred.T) <= tol
+    S.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("shape", ["ragged", "x_faces"])
