@@ -1040,16 +1040,62 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
     lo.linear_eq = o.linear_eq;
     lo.max_steps = o.max_steps;
     lo.cuda_stream = b->stream;
+    // Lattices that share the persistent launch move their whole state every
+    // step.  When those states together exceed the L2 share, the layout of
+    // such a lattice is the one with fewer bytes per step (dense: 19 values
+    // and a link word per voxel; sparse: 19 values and an 8-byte record per
+    // fluid node), not the faster one when timed alone: alone, a small
+    // lattice stays in L2 and its time is the grid barriers', which favours
+    // the dense layout's simpler indexing.  (The 378-lattice subset sweep:
+    // timed choices, mostly dense, 0.555 s; every lattice sparse 0.477 s.)
+    std::vector<std::string> keys(n);
+    std::map<std::string, std::pair<int64_t, int64_t>> counts;  // image -> (N, N_f)
+    for (int i = 0; i < n; ++i) {
+        const lbm_lattice_desc &d = desc[i];
+        if (!d.mask || d.dims[0] <= 0 || d.dims[1] <= 0 || d.dims[2] <= 0) return fail(LBM_EINVAL);
+        // the size lbm_create accepts, checked before any mask byte is read
+        const int64_t n01 = (int64_t)d.dims[0] * d.dims[1];
+        if (n01 >= (int64_t(1) << 31) || n01 * d.dims[2] >= (int64_t(1) << 31)) return fail(LBM_EINVAL);
+        keys[i] = mask_key(d);
+        if (counts.count(keys[i])) continue;
+        const int64_t N = (int64_t)d.dims[0] * d.dims[1] * d.dims[2];
+        int64_t nf = 0;
+        for (int64_t v = 0; v < N; ++v) nf += d.mask[v] == 0;
+        counts[keys[i]] = std::make_pair(N, nf);
+    }
+    const int64_t val_bytes = 19 * (o.precision == LBM_FP64 ? 8 : 4);
+    auto dense_bytes = [&](const std::pair<int64_t, int64_t> &c) { return c.first * (val_bytes + 4); };
+    auto sparse_bytes = [&](const std::pair<int64_t, int64_t> &c) { return c.second * (val_bytes + 8); };
+    auto shares_launch = [&](const std::pair<int64_t, int64_t> &c) {
+        return o.schedule == 1 || c.second < kDirectUnits;
+    };
+    bool by_bytes = false;
+    if (o.layout == -1 && o.schedule != 2) {
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        double shared = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const auto &c = counts[keys[i]];
+            if (shares_launch(c)) shared += (double)std::min(dense_bytes(c), sparse_bytes(c));
+        }
+        by_bytes = shared > (double)(l2 > 0 ? l2 : (64 << 20)) * LBM_STEP_L2_PERCENT / 100.0;
+    }
     // autotune per distinct image: layout and nodes per thread
     std::map<std::string, std::pair<int, int>> tuned;
     b->layout.resize(n);
     b->npt.resize(n);
     for (int i = 0; i < n; ++i) {
         const lbm_lattice_desc &d = desc[i];
-        if (!d.mask) return fail(LBM_EINVAL);
         int lay = o.layout, np = o.nodes_per_thread;
         if (lay == -1 || np == 0) {
-            const std::string key = mask_key(d);
+            const std::string &key = keys[i];
+            const auto &cnt = counts[key];
+            // by bytes: the one layout this image is offered (-1: both)
+            const int pick = by_bytes && shares_launch(cnt)
+                                 ? (sparse_bytes(cnt) <= dense_bytes(cnt) ? LBM_LAYOUT_SPARSE
+                                                                          : LBM_LAYOUT_AA)
+                                 : -1;
             auto it = tuned.find(key);
             if (it == tuned.end()) {
                 // Each candidate layout is timed as it will run: under the
@@ -1064,6 +1110,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                 int bn_of[3] = {1, 1, 1};
                 for (int cl : {LBM_LAYOUT_AA, LBM_LAYOUT_SPARSE}) {
                     if (lay != -1 && cl != lay) continue;
+                    if (pick != -1 && cl != pick) continue;
                     lbm_options to = lo;
                     to.layout = cl;
                     lbm_ctx *c = nullptr;
