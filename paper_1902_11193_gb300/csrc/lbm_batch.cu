@@ -119,7 +119,9 @@ __device__ bool grid_sync(GridBar *bar, unsigned nblocks, uint64_t timeout_ns, b
 #define LBM_BATCH_MIN_BLOCKS 3
 #endif
 
-template <typename S>
+// Idx: type of the sparse population offsets, uint32_t unless a lattice of
+// the launch has 19 units or more per 2^32 (as in the single-lattice kernels).
+template <typename S, typename Idx>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_BATCH_MIN_BLOCKS) k_batch(const BatchLat *__restrict__ lats,
                                                const Tile *__restrict__ tiles,
                                                const int *__restrict__ ntiles_p,
@@ -155,11 +157,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_BATCH_MIN_BLOCKS
                     if (L.layout == LBM_LAYOUT_SPARSE) {
                         fl = true;
                         if (odd)
-                            aa_sparse_update<S, true, size_t, StoreL2<S>>(
+                            aa_sparse_update<S, true, Idx, StoreL2<S>>(
                                 A, L.sm, L.units, u, load_chk(L.sm.nb, u, L.units, L.sm.flag), p,
                                 1.f, 1.f, jx, jy, jz);
                         else
-                            aa_sparse_update<S, false, size_t, StoreL2<S>>(
+                            aa_sparse_update<S, false, Idx, StoreL2<S>>(
                                 A, L.sm, L.units, u, make_uint2(0u, 0u), p, 1.f, 1.f, jx, jy, jz);
                     } else {
                         const uint32_t w = L.lw[u];
@@ -444,6 +446,7 @@ struct lbm_batch {
     std::vector<cudaEvent_t> side_done;
     cudaEvent_t fork;
     bool side_tried;  // side streams created (or their creation failed) once
+    bool wide;        // a lattice needs 64-bit offsets: the persistent kernel takes them
 };
 
 extern "C" {
@@ -514,14 +517,30 @@ BatchLat make_lat(const lbm_ctx *c, int npt) {
 
 int ntiles_of(const BatchLat &L) { return (int)((L.units + kTileThreads * L.npt - 1) / (kTileThreads * L.npt)); }
 
+// The persistent kernel for a precision and offset width.
+const void *batch_kernel(int precision, bool wide) {
+    if (precision == LBM_FP64)
+        return wide ? (const void *)k_batch<double, size_t> : (const void *)k_batch<double, uint32_t>;
+    return wide ? (const void *)k_batch<float, size_t> : (const void *)k_batch<float, uint32_t>;
+}
+
+// Whether lattice L needs 64-bit population offsets.
+bool wide_lat(const BatchLat &L) { return 19 * (uint64_t)L.units >= (uint64_t(1) << 32); }
+
+// Cooperative grid: every block resident, for either offset width.
 int coop_grid(int precision) {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, per = 1 << 30;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (precision == LBM_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<double>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 256, 0);
+    for (const bool wide : {false, true}) {
+        int p = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, batch_kernel(precision, wide), 256, 0) !=
+            cudaSuccess) {
+            p = 0;
+            cudaGetLastError();
+        }
+        per = p < per ? p : per;
+    }
     return sms * (per > 0 ? per : 1);
 }
 
@@ -891,8 +910,7 @@ cudaError_t enqueue_chunk(lbm_batch *b) {
     int nmeas = b->opt.stop_rule == 1 ? 3 : 2;
     void *args[] = {&b->d_lats, &b->d_tiles, &b->d_ntiles, &b->d_steps, &K, &nmeas,
                     &b->d_tile_part, &b->max_tiles, &b->d_bar, &b->timeout_ns};
-    const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
-                                                  : (const void *)k_batch<float>;
+    const void *fn = batch_kernel(b->opt.precision, b->wide);
     e = cudaLaunchCooperativeKernel(fn, dim3(b->grid), dim3(kTileThreads), args, 0, b->stream);
     if (e != cudaSuccess) return e;
     k_batch_finalize<<<b->n, 1024, 0, b->stream>>>(b->d_lats, b->d_lat_tiles, b->d_tile_part,
@@ -935,8 +953,7 @@ float time_candidate(lbm_batch *b, lbm_ctx *c, int npt, int steps) {
         int maxt = nt;
         int nmeas = 2;
         void *args[] = {&d_l, &d_t, &d_n, &d_s, &steps, &nmeas, &d_p, &maxt, &d_b, &b->timeout_ns};
-        const void *fn = b->opt.precision == LBM_FP64 ? (const void *)k_batch<double>
-                                                      : (const void *)k_batch<float>;
+        const void *fn = batch_kernel(b->opt.precision, wide_lat(L));
         cudaEventRecord(e0, b->stream);
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileThreads), args, 0, b->stream);
         cudaEventRecord(e1, b->stream);
@@ -1195,6 +1212,7 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
         b->goff.push_back(ngroups);
         ngroups += groups_of(lats[i]);
         if (!b->solo[i]) total_tiles += ntiles_of(lats[i]);
+        if (!b->solo[i] && wide_lat(lats[i])) b->wide = true;
         std::vector<Tile> ev, od;
         step_tiles_of(lats[i], i, ev, od);
         step_tiles += ev.size() + od.size();
