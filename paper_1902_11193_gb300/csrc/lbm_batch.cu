@@ -1140,6 +1140,11 @@ int lbm_batch_create(lbm_batch **out, int32_t n, const lbm_lattice_desc *desc,
                     for (int cn : {1, 2}) {
                         if (np != 0 && cn != np) continue;
                         if (o.solo == 2) continue;
+                        // layout by bytes, sparse: the launch is bound by DRAM
+                        // traffic, where two units per thread keep more loads
+                        // in flight (the subset: 0.447 -> 0.431 s); timed
+                        // alone, in L2, one unit per thread looked faster
+                        if (pick == LBM_LAYOUT_SPARSE && np == 0 && cn != 2) continue;
                         time_candidate(b, c, cn, 2);  // warm-up
                         const float ms = time_candidate(b, c, cn, 8);
                         if (ms < best_here) {
